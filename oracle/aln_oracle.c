@@ -1,0 +1,631 @@
+/*
+ * aln_oracle.c -- plain, slow, obviously-correct CPU oracle for the BWA-aln
+ * inexact search over an FM-index, as used by BarraCUDA.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is compiled into its own shared library
+ * and is loaded by the tests, by the smoke check and by the benchmark's
+ * CPU-baseline leg.  The product library never links, includes or calls it, and
+ * it shares no code, header or table with the CUDA path.
+ *
+ * What it follows (paper: "Genetically Improved BarraCUDA", Sec. 2 "NextGen DNA
+ * Sequence Alignment"):
+ *  - the index groups all suffixes that share a prefix into one contiguous
+ *    range, so that extending the prefix by a base maps a range to a sub-range
+ *    (index principle, Sec. 2);
+ *  - lookup keeps a lower and an upper pointer that every processed base
+ *    updates from index data; their distance is the number of matching
+ *    positions, and crossed pointers mean no match (backward search, Sec. 2);
+ *  - for non-exact matches the search backs up and tries alternatives
+ *    (bounded backtracking, Sec. 2).
+ * The paper gives no finer detail.  The D lower-bound array, the gap limits, the
+ * seed rule, the strata and the counts follow BWA's short-read method as read in
+ * the project's design notes; each rule is stated where it is implemented.
+ *
+ * Conventions.  Text X over codes A0 C1 G2 T3 (N is replaced before indexing);
+ * Xr = X reversed.  For a text Y, SA and B (the BWT) are over Y$ ($ smallest),
+ * C[c] = number of symbols < c in Y, Occ(c, r) = number of c in B[0..r].
+ * Extending the closed interval [k, l] by c gives
+ *     k' = C[c] + Occ(c, k-1) + 1,   l' = C[c] + Occ(c, l),
+ * empty iff k' > l'.  The empty string has the interval [0, n].
+ *
+ * Parity status: every function here is pinned by tests (brute force over all
+ * alignments on tiny texts, exact-match counts, Hamming scans, LF inversion,
+ * a hand-worked example, D-safety); none is "parity unpinned".
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define OCK 64            /* Occ checkpoint spacing (rows) */
+#define SYM_DOLLAR 4
+#define READ_MAX 255      /* longest read searched; longer reads are flagged */
+#define Z_MAX 7           /* largest per-read difference limit accepted */
+
+/* result flags (same meaning as the product's, defined independently) */
+#define F_HIT_OVERFLOW 0x01
+#define F_READ_TOO_LONG 0x08
+#define F_BAD_LIMIT 0x10
+
+typedef struct {
+    uint64_t n;        /* text length without $ */
+    uint8_t *text;     /* codes 0..3, length n */
+    uint32_t *sa;      /* n+1 suffix starts in sorted order */
+    uint8_t *bwt;      /* n+1 symbols, SYM_DOLLAR at the primary row */
+    uint32_t *ck;      /* ck[4*b + c] = count of c in bwt[0 .. b*OCK-1] */
+    uint64_t C[4];
+    uint64_t primary;
+} otext;
+
+typedef struct {
+    otext t[2];        /* t[0] = X, t[1] = Xr */
+} orc_index;
+
+/* ------------------------------------------------------------ N replacement */
+
+/* SplitMix64 output function (Steele, Lea, Flood 2014) on state x + golden. */
+static uint64_t mix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* ------------------------------------------------------------ suffix sort */
+
+static const uint8_t *g_sort_text;
+static uint64_t g_sort_n;
+
+/* Compare suffixes i and j of text$: byte-wise, the shorter is smaller on a tie. */
+static int suffix_cmp(uint32_t i, uint32_t j)
+{
+    uint64_t li = g_sort_n - i, lj = g_sort_n - j;
+    uint64_t m = li < lj ? li : lj;
+    int c = memcmp(g_sort_text + i, g_sort_text + j, m);
+    if (c) return c;
+    return li < lj ? -1 : (li > lj ? 1 : 0);
+}
+
+static int qsort_cmp(const void *a, const void *b)
+{
+    return suffix_cmp(*(const uint32_t *)a, *(const uint32_t *)b);
+}
+
+typedef struct { uint32_t *a; uint64_t len; } sort_job;
+
+static void *sort_worker(void *p)
+{
+    sort_job *j = (sort_job *)p;
+    qsort(j->a, j->len, sizeof(uint32_t), qsort_cmp);
+    return NULL;
+}
+
+typedef struct { const uint32_t *a; uint64_t na; const uint32_t *b; uint64_t nb; uint32_t *out; } merge_job;
+
+static void *merge_worker(void *p)
+{
+    merge_job *j = (merge_job *)p;
+    uint64_t x = 0, y = 0, o = 0;
+    while (x < j->na && y < j->nb)
+        j->out[o++] = (suffix_cmp(j->a[x], j->b[y]) <= 0) ? j->a[x++] : j->b[y++];
+    while (x < j->na) j->out[o++] = j->a[x++];
+    while (y < j->nb) j->out[o++] = j->b[y++];
+    return NULL;
+}
+
+/* Naive suffix sort of text$ (text of length n): qsort of all suffix starts
+ * with the byte-wise comparator, split over threads and merged pairwise. */
+static int naive_sa(const uint8_t *text, uint64_t n, uint32_t *sa, int nthreads)
+{
+    g_sort_text = text;
+    g_sort_n = n;
+    sa[0] = (uint32_t)n;                 /* the suffix "$" is the smallest */
+    uint32_t *a = sa + 1;
+    for (uint64_t i = 0; i < n; i++) a[i] = (uint32_t)i;
+    if (nthreads < 1) nthreads = 1;
+    if ((uint64_t)nthreads > n / 4096 + 1) nthreads = (int)(n / 4096 + 1);
+    int parts = 1;
+    while (parts * 2 <= nthreads) parts *= 2;
+    uint64_t *bnd = (uint64_t *)malloc((parts + 1) * sizeof(uint64_t));
+    for (int p = 0; p <= parts; p++) bnd[p] = n * (uint64_t)p / parts;
+    pthread_t *th = (pthread_t *)malloc(parts * sizeof(pthread_t));
+    sort_job *sj = (sort_job *)malloc(parts * sizeof(sort_job));
+    for (int p = 0; p < parts; p++) {
+        sj[p].a = a + bnd[p];
+        sj[p].len = bnd[p + 1] - bnd[p];
+        pthread_create(&th[p], NULL, sort_worker, &sj[p]);
+    }
+    for (int p = 0; p < parts; p++) pthread_join(th[p], NULL);
+    uint32_t *tmp = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+    if (!tmp) return -1;
+    uint32_t *src = a, *dst = tmp;
+    merge_job *mj = (merge_job *)malloc(parts * sizeof(merge_job));
+    for (int width = 1; width < parts; width *= 2) {
+        int jobs = 0;
+        for (int p = 0; p < parts; p += 2 * width) {
+            uint64_t lo = bnd[p], mid = bnd[p + width], hi = bnd[p + 2 * width];
+            mj[jobs].a = src + lo; mj[jobs].na = mid - lo;
+            mj[jobs].b = src + mid; mj[jobs].nb = hi - mid;
+            mj[jobs].out = dst + lo;
+            pthread_create(&th[jobs], NULL, merge_worker, &mj[jobs]);
+            jobs++;
+        }
+        for (int q = 0; q < jobs; q++) pthread_join(th[q], NULL);
+        uint32_t *s = src; src = dst; dst = s;
+    }
+    if (src != a) memcpy(a, src, n * sizeof(uint32_t));
+    free(tmp); free(mj); free(sj); free(th); free(bnd);
+    return 0;
+}
+
+/* ------------------------------------------------------------ index */
+
+static int build_text(otext *t, const uint8_t *codes, uint64_t n, int nthreads)
+{
+    t->n = n;
+    t->text = (uint8_t *)malloc(n ? n : 1);
+    t->sa = (uint32_t *)malloc((n + 1) * sizeof(uint32_t));
+    t->bwt = (uint8_t *)malloc(n + 1);
+    uint64_t nck = (n + 1) / OCK + 2;
+    t->ck = (uint32_t *)calloc(4 * nck, sizeof(uint32_t));
+    if (!t->text || !t->sa || !t->bwt || !t->ck) return -1;
+    memcpy(t->text, codes, n);
+    if (naive_sa(t->text, n, t->sa, nthreads)) return -1;
+    /* B[r] = Y[SA[r]-1], or $ where SA[r] = 0 */
+    for (uint64_t r = 0; r <= n; r++) {
+        uint32_t s = t->sa[r];
+        if (s == 0) { t->bwt[r] = SYM_DOLLAR; t->primary = r; }
+        else t->bwt[r] = t->text[s - 1];
+    }
+    /* C[c] = number of symbols smaller than c in Y */
+    uint64_t cnt[4] = {0, 0, 0, 0};
+    for (uint64_t i = 0; i < n; i++) cnt[t->text[i]]++;
+    t->C[0] = 0;
+    for (int c = 1; c < 4; c++) t->C[c] = t->C[c - 1] + cnt[c - 1];
+    /* checkpoints: plain running counts */
+    uint32_t run[4] = {0, 0, 0, 0};
+    for (uint64_t r = 0; r <= n + 1; r++) {
+        if (r % OCK == 0) for (int c = 0; c < 4; c++) t->ck[4 * (r / OCK) + c] = run[c];
+        if (r <= n && t->bwt[r] < 4) run[t->bwt[r]]++;
+    }
+    return 0;
+}
+
+/* Occ(c, r): number of c in B[0..r]; r = -1 gives 0. */
+static uint64_t occ(const otext *t, int c, int64_t r)
+{
+    if (r < 0) return 0;
+    uint64_t rows = (uint64_t)r + 1;
+    uint64_t b = rows / OCK;
+    uint64_t v = t->ck[4 * b + c];
+    for (uint64_t i = b * OCK; i < rows; i++) v += (t->bwt[i] == c);
+    return v;
+}
+
+/* Extend [k, l] by c (prepend c to the pattern).  Returns 1 if non-empty. */
+static int lf_extend(const otext *t, int c, uint64_t k, uint64_t l, uint64_t *k2, uint64_t *l2)
+{
+    uint64_t a = t->C[c] + occ(t, c, (int64_t)k - 1) + 1;
+    uint64_t b = t->C[c] + occ(t, c, (int64_t)l);
+    *k2 = a;
+    *l2 = b;
+    return a <= b;
+}
+
+orc_index *orc_build(const uint8_t *codes, uint64_t n, uint64_t n_seed, int nthreads)
+{
+    if (n >= 0xFFFFFFFFULL) return NULL;
+    orc_index *ix = (orc_index *)calloc(1, sizeof(orc_index));
+    uint8_t *x = (uint8_t *)malloc(n ? n : 1);
+    uint8_t *xr = (uint8_t *)malloc(n ? n : 1);
+    if (!ix || !x || !xr) return NULL;
+    /* every N (code 4, or anything above 3) becomes mix64(n_seed ^ pos) & 3 */
+    for (uint64_t i = 0; i < n; i++)
+        x[i] = codes[i] < 4 ? codes[i] : (uint8_t)(mix64(n_seed ^ i) & 3);
+    for (uint64_t i = 0; i < n; i++) xr[i] = x[n - 1 - i];
+    if (build_text(&ix->t[0], x, n, nthreads) || build_text(&ix->t[1], xr, n, nthreads)) return NULL;
+    free(x);
+    free(xr);
+    return ix;
+}
+
+void orc_free(orc_index *ix)
+{
+    if (!ix) return;
+    for (int w = 0; w < 2; w++) {
+        free(ix->t[w].text); free(ix->t[w].sa); free(ix->t[w].bwt); free(ix->t[w].ck);
+    }
+    free(ix);
+}
+
+uint64_t orc_n(const orc_index *ix) { return ix->t[0].n; }
+void orc_get_text(const orc_index *ix, int w, uint8_t *out) { memcpy(out, ix->t[w].text, ix->t[w].n); }
+void orc_get_sa(const orc_index *ix, int w, uint32_t *out) { memcpy(out, ix->t[w].sa, (ix->t[w].n + 1) * 4); }
+void orc_get_bwt(const orc_index *ix, int w, uint8_t *out) { memcpy(out, ix->t[w].bwt, ix->t[w].n + 1); }
+void orc_get_C(const orc_index *ix, int w, uint64_t *out) { memcpy(out, ix->t[w].C, 4 * sizeof(uint64_t)); }
+uint64_t orc_primary(const orc_index *ix, int w) { return ix->t[w].primary; }
+uint64_t orc_occ(const orc_index *ix, int w, int c, int64_t r) { return occ(&ix->t[w], c, r); }
+
+/* Exact backward search of pattern p[0..len-1] in text w: the pattern is
+ * extended from its last symbol to its first.  Returns 1 and [k, l] if present. */
+int orc_exact(const orc_index *ix, int w, const uint8_t *p, int len, uint64_t *k, uint64_t *l)
+{
+    const otext *t = &ix->t[w];
+    uint64_t a = 0, b = t->n;
+    for (int i = len - 1; i >= 0; i--) {
+        if (p[i] > 3) return 0;
+        if (!lf_extend(t, p[i], a, b, &a, &b)) return 0;
+    }
+    *k = a;
+    *l = b;
+    return 1;
+}
+
+/* ------------------------------------------------------------ search */
+
+typedef struct {
+    int z;               /* default difference limit (used when no per-read z) */
+    int max_gapo, max_gape;
+    int seed_len, seed_z;
+    int indel_end_skip;  /* e */
+    int hit_cap;
+    int strata;          /* 0 = BEST1, 1 = FULL */
+    int use_d;           /* 1 = prune with D, 0 = D taken as all zero */
+} orc_params;
+
+typedef struct {         /* one reported hit */
+    uint32_t k, l;
+    uint16_t aligned_len;
+    uint8_t strand, n_diff, n_mm, n_gapo, n_gape, pad;
+} orc_hit;
+
+typedef struct {
+    uint32_t c0, c1;
+    uint8_t n_hits, flags, d_best, pad;
+} orc_res;
+
+typedef struct {
+    const orc_index *ix;
+    const otext *I;        /* index searched for this strand */
+    uint8_t q[READ_MAX];   /* processed symbols */
+    int m;
+    int D[READ_MAX + 1];
+    int budget;
+    int strand;
+    const orc_params *p;
+    orc_hit *cand;
+    int n_cand, cap_cand;
+    uint64_t lookups;
+} ctx_t;
+
+enum { OP_M = 0, OP_I = 1, OP_D = 2 };
+
+/* witness order: (diffs, n_gapo, n_gape, n_mm, aligned_len) */
+static int witness_less(const orc_hit *a, const orc_hit *b)
+{
+    if (a->n_diff != b->n_diff) return a->n_diff < b->n_diff;
+    if (a->n_gapo != b->n_gapo) return a->n_gapo < b->n_gapo;
+    if (a->n_gape != b->n_gape) return a->n_gape < b->n_gape;
+    if (a->n_mm != b->n_mm) return a->n_mm < b->n_mm;
+    return a->aligned_len < b->aligned_len;
+}
+
+/* Record a candidate; equal (strand, k, l) merge keeping the minimal witness. */
+static void record(ctx_t *c, uint64_t k, uint64_t l, int n_mm, int n_gapo, int n_gape, int alen)
+{
+    orc_hit h;
+    memset(&h, 0, sizeof h);
+    h.k = (uint32_t)k; h.l = (uint32_t)l; h.strand = (uint8_t)c->strand;
+    h.n_mm = (uint8_t)n_mm; h.n_gapo = (uint8_t)n_gapo; h.n_gape = (uint8_t)n_gape;
+    h.n_diff = (uint8_t)(n_mm + n_gapo + n_gape); h.aligned_len = (uint16_t)alen;
+    for (int i = 0; i < c->n_cand; i++) {
+        orc_hit *o = &c->cand[i];
+        if (o->strand == h.strand && o->k == h.k && o->l == h.l) {
+            if (witness_less(&h, o)) *o = h;
+            return;
+        }
+    }
+    if (c->n_cand == c->cap_cand) {
+        c->cap_cand = c->cap_cand ? 2 * c->cap_cand : 64;
+        c->cand = (orc_hit *)realloc(c->cand, c->cap_cand * sizeof(orc_hit));
+    }
+    c->cand[c->n_cand++] = h;
+}
+
+/*
+ * Depth-first enumeration of all edit transcripts of the processed symbols
+ * q[0..m-1] within the budget.  State: i symbols consumed, interval [k, l] of
+ * the target built so far, the counts, and the last operation (for telling a
+ * gap open from a gap extension).
+ *  - match / mismatch: extend by each base b; b = q[i] is a match (an N never
+ *    matches), any other b is a mismatch;
+ *  - insertion: consume q[i] without extending, allowed for e <= i <= m-1-e;
+ *  - deletion: extend by b without consuming, placed before read index i,
+ *    allowed for max(e,1) <= i <= m-max(e,1);
+ *  - a run of insertions (or of deletions) of length g costs one gap open and
+ *    g-1 gap extensions, and g differences;
+ *  - seed: an operation at read index i < seed_len (a deletion placed before
+ *    index i) adds one seed difference, limited by seed_z when seed_len > 0;
+ *  - pruning: stop when budget - diffs < D[i] (D is a lower bound on the
+ *    differences needed by q[i..m-1]).
+ * A node at i = m with a non-empty target is a candidate hit.
+ */
+static void dfs(ctx_t *c, int i, uint64_t k, uint64_t l, int n_mm, int n_gapo, int n_gape,
+                int n_ins, int n_del, int seed, int last)
+{
+    const orc_params *p = c->p;
+    int diffs = n_mm + n_gapo + n_gape;
+    if (c->budget - diffs < c->D[i]) return;
+    if (i == c->m) {
+        int alen = i + n_del - n_ins;
+        if (alen >= 1) record(c, k, l, n_mm, n_gapo, n_gape, alen);
+        return;
+    }
+    int m = c->m, e = p->indel_end_skip;
+    int in_seed = (p->seed_len > 0 && i < p->seed_len);
+    int seed_ok = !in_seed || (seed + 1 <= p->seed_z);
+    int seed2 = seed + in_seed;
+    uint64_t kk[4], ll[4];
+    int ne[4];
+    c->lookups += 2; /* one 4-symbol Occ evaluation at rows k-1 and l */
+    for (int b = 0; b < 4; b++) ne[b] = lf_extend(c->I, b, k, l, &kk[b], &ll[b]);
+    /* match and mismatches */
+    for (int b = 0; b < 4; b++) {
+        if (!ne[b]) continue;
+        if (c->q[i] == b)
+            dfs(c, i + 1, kk[b], ll[b], n_mm, n_gapo, n_gape, n_ins, n_del, seed, OP_M);
+        else if (seed_ok)
+            dfs(c, i + 1, kk[b], ll[b], n_mm + 1, n_gapo, n_gape, n_ins, n_del, seed2, OP_M);
+    }
+    /* insertion of q[i] */
+    if (seed_ok && i >= e && i <= m - 1 - e) {
+        if (last == OP_I) {
+            if (n_gape + 1 <= p->max_gape)
+                dfs(c, i + 1, k, l, n_mm, n_gapo, n_gape + 1, n_ins + 1, n_del, seed2, OP_I);
+        } else if (n_gapo + 1 <= p->max_gapo) {
+            dfs(c, i + 1, k, l, n_mm, n_gapo + 1, n_gape, n_ins + 1, n_del, seed2, OP_I);
+        }
+    }
+    /* deletion of a target base before read index i */
+    int e1 = e < 1 ? 1 : e;
+    if (seed_ok && i >= e1 && i <= m - e1) {
+        for (int b = 0; b < 4; b++) {
+            if (!ne[b]) continue;
+            if (last == OP_D) {
+                if (n_gape + 1 <= p->max_gape)
+                    dfs(c, i, kk[b], ll[b], n_mm, n_gapo, n_gape + 1, n_ins, n_del + 1, seed2, OP_D);
+            } else if (n_gapo + 1 <= p->max_gapo) {
+                dfs(c, i, kk[b], ll[b], n_mm, n_gapo + 1, n_gape, n_ins, n_del + 1, seed2, OP_D);
+            }
+        }
+    }
+}
+
+/*
+ * D array for the processed symbols q[0..m-1] against the text of `other`:
+ * scan from the far end, extending the segment q[j..] one symbol at a time
+ * (a symbol is prepended, so the segment is matched in the same orientation as
+ * the search target); when it no longer occurs (or the symbol is N) count one
+ * difference and restart with an empty segment.  D[j] = count after symbol j,
+ * D[m] = 0.  Each disjoint failed segment needs at least one difference.
+ */
+static uint64_t dscan(const otext *other, const uint8_t *q, int m, int *D)
+{
+    uint64_t look = 0;
+    uint64_t k = 0, l = other->n;
+    int cnt = 0;
+    D[m] = 0;
+    for (int j = m - 1; j >= 0; j--) {
+        int ok = 0;
+        if (q[j] < 4) {
+            look += 2;
+            ok = lf_extend(other, q[j], k, l, &k, &l);
+        }
+        if (!ok) {
+            cnt++;
+            k = 0;
+            l = other->n;
+        }
+        D[j] = cnt;
+    }
+    return look;
+}
+
+/* Strand setup: strand 0 searches q = W on the index of Xr (D from X);
+ * strand 1 searches q = complement(W) on the index of X (D from Xr).  Both
+ * process the read from its 5' end. */
+static void setup_strand(ctx_t *c, const orc_index *ix, const uint8_t *w, int m, int strand)
+{
+    c->strand = strand;
+    c->m = m;
+    for (int i = 0; i < m; i++) {
+        uint8_t b = w[i];
+        c->q[i] = (b > 3) ? 4 : (strand ? (uint8_t)(3 - b) : b);
+    }
+    c->I = &ix->t[strand ? 0 : 1];
+}
+
+static int cand_order(const void *a, const void *b)
+{
+    const orc_hit *x = (const orc_hit *)a, *y = (const orc_hit *)b;
+    if (x->n_diff != y->n_diff) return x->n_diff < y->n_diff ? -1 : 1;
+    if (x->strand != y->strand) return x->strand < y->strand ? -1 : 1;
+    if (x->k != y->k) return x->k < y->k ? -1 : 1;
+    if (x->l != y->l) return x->l < y->l ? -1 : 1;
+    return 0;
+}
+
+/* Run both strands at one budget; returns the number of candidates. */
+static int search_pass(ctx_t c[2], int budget)
+{
+    for (int s = 0; s < 2; s++) {
+        c[s].budget = budget;
+        c[s].n_cand = 0;
+        c[s].lookups = 0;
+        dfs(&c[s], 0, 0, c[s].I->n, 0, 0, 0, 0, 0, 0, OP_M);
+    }
+    return c[0].n_cand + c[1].n_cand;
+}
+
+/* Align one read; writes res and up to hit_cap hits; returns canonical lookups. */
+static uint64_t align_one(const orc_index *ix, const uint8_t *w, int m, int z, const orc_params *p,
+                          orc_res *res, orc_hit *hits, ctx_t c[2])
+{
+    memset(res, 0, sizeof *res);
+    res->d_best = 255;
+    if (m > READ_MAX) { res->flags |= F_READ_TOO_LONG; return 0; }
+    if (z > Z_MAX) { res->flags |= F_BAD_LIMIT; return 0; }
+    uint64_t look = 0;
+    for (int s = 0; s < 2; s++) {
+        c[s].p = p;
+        c[s].ix = ix;
+        setup_strand(&c[s], ix, w, m, s);
+        const otext *other = &ix->t[s ? 1 : 0];
+        look += dscan(other, c[s].q, m, c[s].D);
+        if (!p->use_d) for (int i = 0; i <= m; i++) c[s].D[i] = 0;
+    }
+    int final_budget = -1;
+    if (p->strata == 1) {
+        final_budget = z;
+        search_pass(c, z);
+    } else {
+        /* BEST1: iterative deepening 0, 1, ... to the first budget with a hit
+         * (= d_best), then one pass at min(z, d_best + 1). */
+        for (int b = 0; b <= z; b++) {
+            if (search_pass(c, b) > 0) {
+                final_budget = b + 1 <= z ? b + 1 : z;
+                if (final_budget != b) search_pass(c, final_budget);
+                break;
+            }
+        }
+        if (final_budget < 0) final_budget = z; /* no hit: the tree at budget z was the last */
+    }
+    look += c[0].lookups + c[1].lookups;
+    int nc = c[0].n_cand + c[1].n_cand;
+    if (nc == 0) return look;
+    orc_hit *all = (orc_hit *)malloc(nc * sizeof(orc_hit));
+    memcpy(all, c[0].cand, c[0].n_cand * sizeof(orc_hit));
+    memcpy(all + c[0].n_cand, c[1].cand, c[1].n_cand * sizeof(orc_hit));
+    int d_best = 255;
+    for (int i = 0; i < nc; i++) if (all[i].n_diff < d_best) d_best = all[i].n_diff;
+    int keep_max = (p->strata == 1) ? z : (d_best + 1 <= z ? d_best + 1 : z);
+    int nk = 0;
+    uint64_t c0 = 0, c1 = 0;
+    for (int i = 0; i < nc; i++) {
+        if (all[i].n_diff > keep_max) continue;
+        uint64_t wdt = (uint64_t)all[i].l - all[i].k + 1;
+        if (all[i].n_diff == d_best) c0 += wdt;
+        else if (all[i].n_diff == d_best + 1) c1 += wdt;
+        all[nk++] = all[i];
+    }
+    qsort(all, nk, sizeof(orc_hit), cand_order);
+    int out = nk < p->hit_cap ? nk : p->hit_cap;
+    if (nk > p->hit_cap) res->flags |= F_HIT_OVERFLOW;
+    memcpy(hits, all, out * sizeof(orc_hit));
+    res->n_hits = (uint8_t)out;
+    res->d_best = (uint8_t)d_best;
+    res->c0 = c0 > 0xFFFFFFFFULL ? 0xFFFFFFFFu : (uint32_t)c0;
+    res->c1 = c1 > 0xFFFFFFFFULL ? 0xFFFFFFFFu : (uint32_t)c1;
+    free(all);
+    return look;
+}
+
+typedef struct {
+    const orc_index *ix;
+    const uint8_t *codes;
+    const uint64_t *off;
+    const uint16_t *len;
+    const uint8_t *z;
+    const orc_params *p;
+    orc_res *res;
+    orc_hit *hits;
+    uint64_t *lookups;
+    uint64_t next, n;
+    pthread_mutex_t *mu;
+} batch_job;
+
+static void *batch_worker(void *arg)
+{
+    batch_job *b = (batch_job *)arg;
+    ctx_t c[2];
+    memset(c, 0, sizeof c);
+    for (;;) {
+        pthread_mutex_lock(b->mu);
+        uint64_t r = b->next;
+        uint64_t hi = r + 16 < b->n ? r + 16 : b->n;
+        b->next = hi;
+        pthread_mutex_unlock(b->mu);
+        if (r >= b->n) break;
+        for (; r < hi; r++) {
+            int z = b->z ? b->z[r] : b->p->z;
+            uint64_t lk = align_one(b->ix, b->codes + b->off[r], b->len[r], z, b->p,
+                                    &b->res[r], b->hits + r * (uint64_t)b->p->hit_cap, c);
+            if (b->lookups) b->lookups[r] = lk;
+        }
+    }
+    free(c[0].cand);
+    free(c[1].cand);
+    return NULL;
+}
+
+/* Align a batch of reads with nthreads host threads.  Reads are codes 0..4,
+ * read r at codes[off[r] .. off[r]+len[r]-1]; z may be NULL (p->z for all).
+ * hits has room for n * hit_cap records; lookups (may be NULL) gets the
+ * canonical Occ-lookup count per read. */
+int orc_align(const orc_index *ix, const uint8_t *codes, const uint64_t *off, const uint16_t *len,
+              const uint8_t *z, uint64_t n, const orc_params *p, int nthreads,
+              orc_res *res, orc_hit *hits, uint64_t *lookups)
+{
+    if (!ix || !p || p->hit_cap < 0 || p->hit_cap > 255) return -1;
+    pthread_mutex_t mu;
+    pthread_mutex_init(&mu, NULL);
+    batch_job job = {ix, codes, off, len, z, p, res, hits, lookups, 0, n, &mu};
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc(nthreads * sizeof(pthread_t));
+    for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, batch_worker, &job);
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&mu);
+    return 0;
+}
+
+/* D array of one read on one strand (for tests). */
+int orc_dscan(const orc_index *ix, int strand, const uint8_t *w, int m, int *D)
+{
+    ctx_t c;
+    memset(&c, 0, sizeof c);
+    if (m > READ_MAX) return -1;
+    setup_strand(&c, ix, w, m, strand);
+    dscan(&ix->t[strand ? 1 : 0], c.q, m, D);
+    return 0;
+}
+
+static int u64_cmp(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y);
+}
+
+/* Forward-strand 0-based start of the target for every row of a hit of width
+ * <= max_width, from the full suffix arrays: strand 0 -> n - SA_Xr[j] - len,
+ * strand 1 -> SA_X[j].  Positions of one hit are sorted ascending and written
+ * at pos[hit_i * max_width ...]; npos[hit_i] = count (0 if the hit is wider). */
+int orc_positions(const orc_index *ix, const orc_hit *h, uint64_t nh, uint32_t max_width,
+                  uint64_t *pos, uint32_t *npos)
+{
+    uint64_t n = ix->t[0].n;
+    for (uint64_t i = 0; i < nh; i++) {
+        uint64_t w = (uint64_t)h[i].l - h[i].k + 1;
+        npos[i] = 0;
+        if (h[i].l < h[i].k || w > max_width) continue;
+        uint64_t *o = pos + i * max_width;
+        for (uint64_t j = 0; j < w; j++) {
+            uint64_t row = h[i].k + j;
+            o[j] = h[i].strand ? ix->t[0].sa[row] : n - ix->t[1].sa[row] - h[i].aligned_len;
+        }
+        qsort(o, w, sizeof(uint64_t), u64_cmp);
+        npos[i] = (uint32_t)w;
+    }
+    return 0;
+}

@@ -1,0 +1,93 @@
+"""The oracle's pins have teeth: each plausible mistake planted in a copy of the
+oracle's C source (an off-by-one, a dropped term, a wrong sign or index, a
+swapped operand) makes at least one pin fail.  The mutants are compiled on the
+CPU into a temporary directory; the committed oracle is untouched."""
+import contextlib
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "aln_oracle.c")
+
+MUTANTS = {
+    "lf_lower_bound_row": ("occ(t, c, (int64_t)k - 1) + 1", "occ(t, c, (int64_t)k) + 1"),
+    "insertion_window": ("i >= e && i <= m - 1 - e", "i >= e && i <= m - e"),
+    "deletion_window": ("i >= e1 && i <= m - e1", "i >= e1 - 1 && i <= m - e1"),
+    "no_gap_extension": ("if (last == OP_I) {", "if (0) {"),
+    "d_prune_off_by_one": ("c->budget - diffs < c->D[i]", "c->budget - diffs <= c->D[i]"),
+    "n_matches_a": ("if (c->q[i] == b)", "if ((c->q[i] & 3) == b)"),
+    "seed_ignores_deletion": ("dfs(c, i, kk[b], ll[b], n_mm, n_gapo + 1, n_gape, n_ins, n_del + 1, seed2, OP_D)",
+                              "dfs(c, i, kk[b], ll[b], n_mm, n_gapo + 1, n_gape, n_ins, n_del + 1, seed, OP_D)"),
+    "witness_gapo_order": ("return a->n_gapo < b->n_gapo", "return a->n_gapo > b->n_gapo"),
+    "c1_stratum": ("all[i].n_diff == d_best + 1", "all[i].n_diff == d_best + 2"),
+    "reverse_not_complemented": ("(strand ? (uint8_t)(3 - b) : b)", "b"),
+    "dscan_overcounts": ("            cnt++;\n", "            cnt += 2;\n"),
+    "dollar_largest": ("return li < lj ? -1 : (li > lj ? 1 : 0);", "return li > lj ? -1 : (li < lj ? 1 : 0);"),
+    "best1_no_second_stratum": ("int keep_max = (p->strata == 1) ? z : (d_best + 1 <= z ? d_best + 1 : z);",
+                                "int keep_max = (p->strata == 1) ? z : d_best;"),
+    "forward_position_offset": ("n - ix->t[1].sa[row] - h[i].aligned_len", "n - ix->t[1].sa[row] - h[i].aligned_len + 1"),
+    "order_strand_before_diffs": ("if (x->n_diff != y->n_diff) return x->n_diff < y->n_diff ? -1 : 1;\n    if (x->strand != y->strand)",
+                                  "if (x->strand != y->strand) return x->strand < y->strand ? -1 : 1;\n    if (x->n_diff != y->n_diff)"),
+    "mismatch_seed_free": ("else if (seed_ok)\n            dfs(c, i + 1, kk[b], ll[b], n_mm + 1, n_gapo, n_gape, n_ins, n_del, seed2, OP_M);",
+                           "else\n            dfs(c, i + 1, kk[b], ll[b], n_mm + 1, n_gapo, n_gape, n_ins, n_del, seed, OP_M);"),
+}
+
+
+def _pin_calls():
+    c = pins.CASES
+    return [
+        pins.test_hand_example,
+        lambda: pins.test_sa_bwt_against_naive_sort(300, 4, 2),
+        lambda: pins.test_exact_interval_is_naive_scan(21),
+        pins.test_z0_is_exact_matching,
+        lambda: pins.test_mismatch_only_is_hamming_scan(2),
+        lambda: pins.test_against_brute_force(*c[1], "FULL"),
+        lambda: pins.test_against_brute_force(*c[3], "BEST1"),
+        lambda: pins.test_against_brute_force(*c[5], "FULL"),
+        pins.test_positions_match_brute_force,
+        pins.test_d_array_properties_and_safety,
+        pins.test_best1_is_full_filtered,
+        pins.test_edge_reads,
+        pins.test_homopolymer_gap_witness,
+        lambda: pins.test_every_position_every_edit(0),
+        lambda: pins.test_every_position_every_edit(2),
+        lambda: pins.test_against_brute_force(*c[2], "FULL"),
+        lambda: pins.test_every_pair_of_edits_in_seed(1),
+    ]
+
+
+@contextlib.contextmanager
+def _oracle_from(path):
+    saved_lib, saved_build = oracle._lib, oracle.build
+    oracle._lib = None
+    oracle.build = lambda force=False: path
+    try:
+        yield
+    finally:
+        oracle._lib, oracle.build = saved_lib, saved_build
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mut = src.replace(old, new, 1)
+    c_path = tmp_path / "mut.c"
+    so_path = tmp_path / "libmut.so"
+    c_path.write_text(mut)
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-D_POSIX_C_SOURCE=200809L", "-shared",
+                           "-fPIC", "-pthread", "-o", str(so_path), str(c_path)])
+    caught = []
+    with _oracle_from(str(so_path)):
+        for call in _pin_calls():
+            try:
+                call()
+            except (AssertionError, ValueError, IndexError):
+                caught.append(call)
+                break
+    assert caught, f"mutant {name} passed every pin"
