@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 BWA-aln inexact FM-index search.
+
+Workload (default): 100 Mbp order-3 Markov reference (41 % GC, 5 % copies of 50
+repeat families), 1 M single-end 100 bp reads (substitutions 0.5 % -> 2 %,
+0.02 % indels of 1-3 bp), z=4, seed 32 with <= 2 seed differences, gap opens
+<= 1, gap extensions <= 6, no indel within 5 bp of an end; BEST1 strata.
+
+A step is one aln_search over the whole 1 M-read batch (both strands, D scans,
+backtracking search, hit reduction).  The headline is the persistent (batched)
+form; the plain one-launch-per-batch form is timed beside it.  L2 is flushed
+(a 512 MiB write) before every timed step.  `--impl reference` times the CPU
+oracle on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reads/s bit-exact vs oracle (batched vs plain, 1 GB300); % HBM roofline; p99 ms"
+BYTES_PER_LOOKUP = 64
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(w, n_sample, threads, seed=7):
+    """Oracle index of the text and its results on a seeded sample of reads."""
+    import oracle
+    t0 = time.time()
+    ox = oracle.OracleIndex(w.text, threads=threads)
+    t_index = time.time() - t0
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(w.reads.n, min(n_sample, w.reads.n), replace=False))
+    sub = w.reads.subset(idx)
+    lim = w.params
+    t0 = time.time()
+    ro, ho, look = ox.align(sub.codes, sub.offsets, sub.lens, sub.z, z_default=lim["z"],
+                            max_gapo=lim["max_gapo"], max_gape=lim["max_gape"],
+                            seed_len=lim["seed_len"], seed_z=lim["seed_z"],
+                            indel_end_skip=lim["indel_end_skip"], hit_cap=32, threads=threads)
+    t_align = time.time() - t0
+    return ox, idx, ro, ho, look, t_index, t_align
+
+
+def run_reference(args):
+    """CPU oracle arm: each step aligns a bounded seeded sample on all host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from synth import workload
+    w = workload(args.workload)
+    threads = oracle.default_threads()
+    ox = oracle.OracleIndex(w.text, threads=threads)
+    lim = w.params
+    rng = np.random.default_rng(11)
+    per_step = args.ref_sample
+
+    def step(i):
+        idx = np.sort(rng.choice(w.reads.n, per_step, replace=False))
+        sub = w.reads.subset(idx)
+        ox.align(sub.codes, sub.offsets, sub.lens, sub.z, z_default=lim["z"], max_gapo=lim["max_gapo"],
+                 max_gape=lim["max_gape"], seed_len=lim["seed_len"], seed_z=lim["seed_z"],
+                 indel_end_skip=lim["indel_end_skip"], hit_cap=32, threads=threads)
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.time()
+    for i in range(args.steps):
+        step(i)
+    dt = time.time() - t0
+    v = per_step * args.steps / dt
+    sample = f"{per_step} seeded reads per step of the {w.reads.n}-read batch"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "reads/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": args.workload, "reads_per_step": per_step},
+        "cpu_baseline": {"value": v, "unit": "reads/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import paper_1505_07855_gb300 as aln
+    from synth import workload
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    t_all = time.time()
+    w = workload(args.workload)
+    lim = w.params
+    n = w.reads.n
+    # index: rank 0 builds and saves, the other replicas load the image
+    t0 = time.time()
+    if ws > 1:
+        path = f"/tmp/aln_bench_{args.workload}.fmi"
+        if rank == 0:
+            aln.Index.build(w.text, kmer_k=args.kmer_k).save(path)
+        torch.distributed.barrier()
+        hix = aln.Index.load(path)
+    else:
+        hix = aln.Index.build(w.text, kmer_k=args.kmer_k)
+    t_build = time.time() - t0
+    dix = hix.to_device(local)
+    al = aln.Aligner(dix)
+    stream = torch.cuda.Stream(device=dev)
+    bases, nmask, offs = aln.pack_reads(w.reads.codes, w.reads.offsets, w.reads.lens)
+    lens = np.ascontiguousarray(w.reads.lens)
+    d = {"bases": torch.from_numpy(bases.view(np.int32)).to(dev),
+         "nmask": torch.from_numpy(nmask.view(np.int32)).to(dev),
+         "offsets": torch.from_numpy(offs.view(np.int64)).to(dev),
+         "lens": torch.from_numpy(lens.view(np.int16)).to(dev), "z": None, "n": n}
+    hit_cap = 32
+    res, hits = al.outputs(n, hit_cap)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    modes = {"persistent": aln.MODE_PERSISTENT, "plain": aln.MODE_PLAIN}
+    params = {k: aln.Params.from_limits(lim, hit_cap=hit_cap, mode=m) for k, m in modes.items()}
+
+    def step(mode):
+        al.search_device(d, params[mode], res, hits, stream)
+
+    with torch.cuda.stream(stream):
+        for mode in modes:
+            for _ in range(args.warmup):
+                flush.zero_()
+                step(mode)
+    torch.cuda.synchronize(dev)
+    times = {}
+    out = {}
+    if ws > 1:
+        torch.distributed.barrier()
+    with Clocks(local) as clk:
+        for mode in modes:
+            evs = []
+            torch.cuda.synchronize(dev)
+            with torch.cuda.stream(stream):
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    step(mode)
+                    e1.record(stream)
+                    evs.append((e0, e1))
+            torch.cuda.synchronize(dev)
+            ms = [a.elapsed_time(b) for a, b in evs]
+            times[mode] = ms
+            out[mode] = (res.cpu().numpy().view(aln.RES_DTYPE)[:n].copy(),
+                         hits.cpu().numpy().view(aln.HIT_DTYPE)[:n * hit_cap].reshape(n, hit_cap).copy())
+    clocks = clk.summary()
+    ms_head = float(np.mean(times["persistent"]))
+    ms_plain = float(np.mean(times["plain"]))
+    if ws > 1:
+        t = torch.tensor([ms_head, ms_plain], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_head, ms_plain = float(t[0]), float(t[1])
+    same = bool(np.array_equal(out["plain"][0], out["persistent"][0]) and
+                np.array_equal(out["plain"][1], out["persistent"][1]))
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    h_bases = torch.from_numpy(bases.view(np.int32)).pin_memory()
+    h_nmask = torch.from_numpy(nmask.view(np.int32)).pin_memory()
+    h_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
+    h_lens = torch.from_numpy(lens.view(np.int16)).pin_memory()
+    h_res = torch.empty(res.numel(), dtype=torch.uint8).pin_memory()
+    h_hits = torch.empty(hits.numel(), dtype=torch.uint8).pin_memory()
+    h2d = sum(x.numel() * x.element_size() for x in (h_bases, h_nmask, h_offs, h_lens))
+    d2h = h_res.numel() + h_hits.numel()
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d["bases"].copy_(h_bases, non_blocking=True)
+            d["nmask"].copy_(h_nmask, non_blocking=True)
+            d["offsets"].copy_(h_offs, non_blocking=True)
+            d["lens"].copy_(h_lens, non_blocking=True)
+            step("persistent")
+            h_res.copy_(res, non_blocking=True)
+            h_hits.copy_(hits, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+    e2e_v = ws * n / (np.mean(e2e_ms) / 1000)
+
+    line = {
+        "metric": METRIC, "value": ws * n / (ms_head / 1000), "unit": "reads/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_head, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "ref_bp": int(w.text.size), "reads_per_step": n,
+                   "read_len": 100, "z": lim["z"], "seed": [lim["seed_len"], lim["seed_z"]],
+                   "strata": "BEST1", "mode": "persistent", "l2": "flushed (512 MiB write) before every step",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single"},
+        "plain": {"value": ws * n / (ms_plain / 1000), "ms_per_step": ms_plain,
+                  "bit_identical_to_persistent": same},
+        "gpu_launches": args.steps,
+        "e2e": {"value": e2e_v, "unit": "reads/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "clocks": clocks,
+        "build_s": t_build,
+    }
+    if rank == 0 and not args.no_oracle:
+        import oracle
+        threads = oracle.default_threads()
+        # size the sample to ~15 s of oracle search on all host cores
+        ox, idx, ro, ho, look, t_index, t_align = oracle_sample(w, 300, threads)
+        rate = len(idx) / max(t_align, 1e-6)
+        target = int(min(max(1000, rate * args.cpu_seconds), 50_000))
+        rng = np.random.default_rng(7)
+        sel = np.sort(rng.choice(n, min(target, n), replace=False))
+        sub = w.reads.subset(sel)
+        t0 = time.time()
+        ro, ho, look = ox.align(sub.codes, sub.offsets, sub.lens, sub.z, z_default=lim["z"],
+                                max_gapo=lim["max_gapo"], max_gape=lim["max_gape"],
+                                seed_len=lim["seed_len"], seed_z=lim["seed_z"],
+                                indel_end_skip=lim["indel_end_skip"], hit_cap=hit_cap, threads=threads)
+        t_align = time.time() - t0
+        cpu_v = sel.size / t_align
+        # parity of the timed outputs on the sample
+        rg, hg = out["persistent"]
+        rg, hg = rg[sel], hg[sel]
+        ok = all(np.array_equal(rg[f], ro[f]) for f in ("c0", "c1", "n_hits", "d_best", "flags"))
+        valid = np.arange(hit_cap)[None, :] < rg["n_hits"][:, None]
+        for f in ("k", "l", "aligned_len", "strand", "n_diff", "n_mm", "n_gapo", "n_gape"):
+            ok = ok and np.array_equal(np.where(valid, hg[f], 0), np.where(valid, ho[f], 0))
+        lookups_per_read = float(look.mean())
+        alg_bytes = lookups_per_read * BYTES_PER_LOOKUP * n
+        peak, src = _peaks()
+        achieved = alg_bytes / (ms_head / 1000) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None, "peak_source": src,
+                            "bytes_per_read": lookups_per_read * BYTES_PER_LOOKUP,
+                            "occ_lookups_per_s": lookups_per_read * n / (ms_head / 1000)}
+        line["cpu_baseline"] = {"value": cpu_v, "unit": "reads/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{sel.size} seeded reads of the {n}-read batch, "
+                                          f"oracle index build ({t_index:.1f} s) not timed"}
+        line["parity"] = {"sampled_reads": int(sel.size), "bit_exact": bool(ok)}
+    line["wall_s"] = time.time() - t_all
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="chr100", choices=["chr100", "tiny36"])
+    ap.add_argument("--kmer-k", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-sample", type=int, default=2000)
+    ap.add_argument("--no-oracle", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

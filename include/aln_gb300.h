@@ -1,0 +1,232 @@
+/*
+ * aln_gb300.h -- C ABI of the GB300 (sm_103a) implementation of the BWA-aln
+ * inexact search over an FM-index, the hot path of BarraCUDA.
+ *
+ * Paper: W. B. Langdon and B. Y. H. Lam, "Genetically Improved BarraCUDA",
+ * UCL RN/15/03 (arXiv:1505.07855).  Sec. 2 ("NextGen DNA Sequence Alignment")
+ * states the problem these calls follow:
+ *   - the reference is indexed once, offline, so that all suffixes with the same
+ *     starting subsequence share one contiguous location      -> fm_index_build
+ *   - the whole index must be held in GPU memory             -> fm_index_to_device
+ *   - each read is looked up with a lower and an upper pointer updated per
+ *     base; their distance is the number of matching positions and crossed
+ *     pointers mean no match; non-exact matches back up and try alternatives
+ *                                                             -> aln_search
+ *   - the pairing stage needs reference positions from the index (Sec. 2 and
+ *     the pipeline description in Sec. 3)                     -> sa_to_pos
+ * Everything finer (D lower-bound pruning, gap and seed limits, strata, counts)
+ * follows BWA's short-read method; the semantics are stated below per call.
+ *
+ * Conventions used by every call:
+ *   base codes A=0 C=1 G=2 T=3 N=4; X = the reference after N replacement,
+ *   Xr = X reversed.  For a text Y, SA and the BWT B are over Y$ ($ smallest),
+ *   C[c] = number of symbols < c in Y and Occ(c, r) = number of c in B[0..r].
+ *   A hit is a closed interval [k, l] of suffix-array rows.  Rows run 0..n.
+ *   Forward-strand hits are intervals in SA_Xr (of the reversed target),
+ *   reverse-strand hits are intervals in SA_X (of the target aligned to the
+ *   reverse complement of the read).  Read indices count from the read's 5' end.
+ *
+ * Every call returns an int status: ALN_OK (0) or a negative ALN_E* code.  No
+ * call throws or aborts.  aln_last_error() returns a message for the calling
+ * thread's last failure.  Device pointers are CUDA device (or managed) memory
+ * on the device the index was uploaded to; "stream" is a cudaStream_t (NULL =
+ * the legacy default stream).
+ */
+#ifndef ALN_GB300_H
+#define ALN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define ALN_OK 0
+#define ALN_EINVAL (-1)    /* bad argument (null pointer, size, limit out of range) */
+#define ALN_ENOMEM (-2)    /* host or device allocation failed / does not fit */
+#define ALN_EDEVICE (-3)   /* a CUDA call failed (message has the CUDA error) */
+#define ALN_ELIMIT (-4)    /* a bounded loop reached its iteration limit */
+#define ALN_EOVERFLOW (-5) /* a caller-provided buffer is too small */
+#define ALN_EIO (-6)       /* file could not be read or written, or is malformed */
+
+/* ---------------------------------------------------------------- limits */
+#define ALN_MAX_READ_LEN 255 /* longer reads get ALN_FLAG_READ_TOO_LONG and no hits */
+#define ALN_MAX_Z 7          /* largest difference limit; larger per-read z is flagged */
+#define ALN_MAX_HIT_CAP 255
+#define ALN_MAX_KMER_K 13
+#define ALN_CAND_CAP 64      /* distinct candidate hits kept per read by the kernels */
+
+/* ---------------------------------------------------------------- per-read flags */
+#define ALN_FLAG_HIT_OVERFLOW 0x01   /* more kept hits than hit_cap: list truncated,
+                                        c0/c1 still count every kept hit */
+#define ALN_FLAG_STACK_OVERFLOW 0x02 /* search stack full: result incomplete */
+#define ALN_FLAG_CAND_OVERFLOW 0x04  /* more than ALN_CAND_CAP distinct candidates:
+                                        result incomplete */
+#define ALN_FLAG_READ_TOO_LONG 0x08  /* len > ALN_MAX_READ_LEN: not searched */
+#define ALN_FLAG_BAD_LIMIT 0x10      /* per-read z > ALN_MAX_Z: not searched */
+#define ALN_FLAG_WORK_LIMIT 0x20     /* per-read expansion limit reached: incomplete */
+#define ALN_FLAG_INCOMPLETE (ALN_FLAG_STACK_OVERFLOW | ALN_FLAG_CAND_OVERFLOW | ALN_FLAG_WORK_LIMIT)
+
+/* ---------------------------------------------------------------- modes */
+#define ALN_MODE_PLAIN 0      /* one launch per batch, one thread per read */
+#define ALN_MODE_PERSISTENT 1 /* one persistent launch; threads pull reads from a device queue */
+#define ALN_STRATA_BEST1 0    /* keep hits with diffs <= min(z, d_best + 1) */
+#define ALN_STRATA_FULL 1     /* keep every hit with diffs <= z */
+
+typedef struct fm_index fm_index;   /* host-resident index (opaque) */
+typedef struct fm_dindex fm_dindex; /* device-resident index image (opaque) */
+
+typedef struct {
+    uint64_t n_seed;    /* every N of the text is indexed as splitmix64(n_seed ^ pos) & 3 */
+    uint32_t sa_sample; /* keep SA[r] for rows r % sa_sample == 0; power of two 1..1024; 0 -> 32 */
+    uint32_t kmer_k;    /* k of the k-mer interval table, 0 = none, <= ALN_MAX_KMER_K */
+    int32_t n_threads;  /* host threads for construction; 0 = all online cores */
+    uint32_t reserved;
+} fm_build_opts;
+
+typedef struct {
+    uint64_t n;          /* text length (without $) */
+    uint64_t primary[2]; /* row of $ in B_X (0) and B_Xr (1) */
+    uint64_t C[2][4];    /* C arrays of X and Xr */
+    uint64_t occ_bytes;  /* bytes of Occ blocks per text: 64 per 192 rows */
+    uint64_t sa_bytes;   /* bytes of sampled SA per text */
+    uint64_t kmer_bytes; /* bytes of k-mer table per text */
+    uint32_t sa_sample;
+    uint32_t kmer_k;
+} fm_index_info_t;
+
+/* Build the index of X and of Xr on the host (Sec. 2: offline encoding).
+ * text: host, n codes 0..4 (N is replaced, anything > 3 counts as N).  n must be
+ * >= 1 and < 2^32 - 1 (row numbers are 32-bit), else ALN_EINVAL.  opts may be
+ * NULL (defaults).  On success *out owns the index; free it with fm_index_free. */
+int fm_index_build(const uint8_t *text, uint64_t n, const fm_build_opts *opts, fm_index **out);
+void fm_index_free(fm_index *idx);
+int fm_index_info(const fm_index *idx, fm_index_info_t *info);
+
+/* Write / read the index image (little-endian binary, magic "ALNFMIX1").
+ * Load returns ALN_EIO on a missing, short or malformed file. */
+int fm_index_save(const fm_index *idx, const char *path);
+int fm_index_load(const char *path, fm_index **out);
+
+/* Copy the index to device memory (Sec. 2: the whole index is held in GPU
+ * memory).  device: CUDA ordinal.  The copy is enqueued on stream and finished
+ * before return.  The library allocates the device image (Occ blocks, sampled SA
+ * and k-mer table of both texts); ALN_ENOMEM if it does not fit.  Free with
+ * fm_dindex_free. */
+int fm_index_to_device(const fm_index *idx, int device, void *stream, fm_dindex **out);
+void fm_dindex_free(fm_dindex *d);
+int fm_dindex_info(const fm_dindex *d, fm_index_info_t *info);
+
+/* A batch of reads in device memory.
+ *   bases : 2-bit packed bases, 16 per 32-bit word, base j of the batch in word
+ *           j/16 at bits 2*(j%16) (low bits first).  An N is stored as any code
+ *           and marked in nmask.
+ *   nmask : 1 bit per base, 32 per word, bit j%32 of word j/32; may be NULL.
+ *   offset: index of the read's first base in the batch's base stream.
+ *   len   : read length in bases (0 allowed: no hits).
+ *   z     : per-read difference limit; NULL = params.z for every read.
+ * aln_pack_reads builds this layout on the host. */
+typedef struct {
+    const uint32_t *bases;
+    const uint32_t *nmask;
+    const uint64_t *offset;
+    const uint16_t *len;
+    const uint8_t *z;
+} aln_batch;
+
+typedef struct {
+    uint8_t z;              /* difference limit (mismatches + gap bases) when batch.z is NULL;
+                               with a per-read z array, an upper bound on it (reads above it
+                               get ALN_FLAG_BAD_LIMIT); sizes the search stack */
+    uint8_t max_gapo;       /* gap opens */
+    uint8_t max_gape;       /* gap extensions; a gap of length g = 1 open + (g-1) extensions */
+    uint8_t seed_len;       /* s: first s read bases form the seed; 0 = no seed */
+    uint8_t seed_z;         /* differences allowed inside the seed */
+    uint8_t indel_end_skip; /* e: no insertion at read index < e or > len-1-e; a deletion
+                               only between read indices with >= max(e,1) bases each side */
+    uint8_t hit_cap;        /* hits written per read, 1..ALN_MAX_HIT_CAP */
+    uint8_t mode;           /* ALN_MODE_* */
+    uint8_t strata;         /* ALN_STRATA_* */
+    uint8_t reserved[3];
+    uint32_t work_limit;    /* node expansions per read before ALN_FLAG_WORK_LIMIT; 0 = 2^24 */
+} aln_params;
+
+/* One hit, 16 bytes.  The witness (n_diff .. aligned_len) is the minimal one,
+ * ordered by (n_diff, n_gapo, n_gape, n_mm, aligned_len), over every valid
+ * transcript whose target has this interval. */
+typedef struct {
+    uint32_t k, l;          /* closed SA interval; width l - k + 1 positions */
+    uint16_t aligned_len;   /* target length */
+    uint8_t strand;         /* 0 forward (interval in SA_Xr), 1 reverse (in SA_X) */
+    uint8_t n_diff;         /* n_mm + n_gapo + n_gape */
+    uint8_t n_mm, n_gapo, n_gape;
+    uint8_t reserved;
+} aln_hit;
+
+/* Per-read result, 12 bytes. */
+typedef struct {
+    uint32_t c0;            /* sum of widths of kept hits with n_diff == d_best */
+    uint32_t c1;            /* sum of widths of kept hits with n_diff == d_best + 1 */
+    uint8_t n_hits;         /* hits written (<= hit_cap) */
+    uint8_t flags;          /* ALN_FLAG_* */
+    uint8_t d_best;         /* fewest differences of any hit; 255 = no hit */
+    uint8_t reserved;
+} aln_read_result;
+
+typedef struct {
+    aln_read_result *reads; /* device, n_reads entries */
+    aln_hit *hits;          /* device, n_reads * hit_cap entries; read r at r * hit_cap */
+} aln_result;
+
+/* Search every read on both strands (Sec. 2: pointer-pair lookup with
+ * backtracking), output per read: its hits sorted by (n_diff, strand, k, l)
+ * and truncated to hit_cap, d_best, c0 and c1.
+ * Result definition: a transcript aligns all of the read (forward strand) or
+ * of its reverse complement (reverse strand) to a non-empty substring T of X
+ * with matches, mismatches (an N always mismatches), insertions (read base not
+ * in T) and deletions (T base not in the read); it is valid iff diffs <= z,
+ * gap opens <= max_gapo, gap extensions <= max_gape, the end window e holds,
+ * and, if seed_len > 0, the differences at read indices < seed_len (a deletion
+ * counts at the read index that follows it) are <= seed_z.  Hits with equal
+ * (strand, k, l) merge.  BEST1 keeps hits with diffs <= min(z, d_best + 1).
+ * All arrays are device memory, written asynchronously on stream; the caller
+ * synchronises.  Returns ALN_EINVAL for bad params, ALN_EDEVICE on a launch
+ * failure, ALN_ELIMIT if the persistent queue did not drain within its bound.
+ * Per-read problems are reported in flags, never by the status. */
+int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
+               const aln_params *params, aln_result *out, void *stream);
+
+#define ALN_POS_TOO_WIDE 0xFFFFFFFFu /* n_pos_out value: hit wider than max_width */
+#define ALN_POS_WALK_LIMIT 0xFFFFFFFEu /* n_pos_out value: an LF walk exceeded its bound */
+
+/* Reference positions of hits (Sec. 2/3: the pairing stage needs positions
+ * from the index).  For hit i of width <= max_width, n_pos_out[i] = width and
+ * pos_out[i*max_width ...] = the forward-strand 0-based starts of the target,
+ * sorted ascending: strand 0 -> n - SA_Xr[j] - aligned_len, strand 1 ->
+ * SA_X[j], for rows j = k..l.  Each SA value comes from the sampled SA after
+ * an LF walk to the nearest sampled row (expected sa_sample steps, bounded by
+ * 64 * sa_sample; a hit with a walk past the bound gets ALN_POS_WALK_LIMIT).
+ * Wider hits get ALN_POS_TOO_WIDE.  hits, pos_out and n_pos_out are device
+ * memory; max_width 1..64.  Asynchronous on stream. */
+int sa_to_pos(const fm_dindex *idx, const aln_hit *hits, uint32_t n_hits, uint32_t max_width,
+              uint64_t *pos_out, uint32_t *n_pos_out, void *stream);
+
+/* Host helper: pack reads (codes 0..4, read r at codes[code_offset[r]] of
+ * length len[r]) back to back into the aln_batch layout.  bases_out needs
+ * ceil(total/16) words, nmask_out ceil(total/32) words (total = sum of len),
+ * offset_out n_reads entries.  Host memory only. */
+int aln_pack_reads(const uint8_t *codes, const uint64_t *code_offset, const uint16_t *len,
+                   uint32_t n_reads, uint32_t *bases_out, uint32_t *nmask_out,
+                   uint64_t *offset_out);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *aln_last_error(void);
+/* Library ABI version (major * 100 + minor). */
+int aln_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALN_GB300_H */

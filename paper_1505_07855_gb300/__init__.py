@@ -1,0 +1,228 @@
+"""GB300-native BWA-aln inexact FM-index search (the hot path of BarraCUDA).
+
+Python binding of the C ABI in include/aln_gb300.h.  PyTorch supplies device
+memory and streams; the index build runs in the library's host C++ and every
+step of the search runs in its sm_103a kernels.  There is no CPU fallback.
+
+Typical use::
+
+    idx = Index.build(text_codes)            # fm_index_build
+    dix = idx.to_device(0)                   # fm_index_to_device
+    al = Aligner(dix)
+    res, hits = al.align(codes, offsets, lens, Params(z=2))   # aln_search
+    pos, npos = al.positions(hits_device, n, 16)              # sa_to_pos
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    ALN_OK, AlnError, CAND_CAP, FLAG_BAD_LIMIT, FLAG_CAND_OVERFLOW, FLAG_HIT_OVERFLOW,
+    FLAG_INCOMPLETE, FLAG_READ_TOO_LONG, FLAG_STACK_OVERFLOW, FLAG_WORK_LIMIT, HIT_DTYPE,
+    MAX_HIT_CAP, MAX_READ_LEN, MAX_Z, MODE_PERSISTENT, MODE_PLAIN, POS_TOO_WIDE, POS_WALK_LIMIT,
+    RES_DTYPE, STRATA_BEST1, STRATA_FULL, check, lib, library_path,
+)
+
+__all__ = ["Index", "DeviceIndex", "Params", "Aligner", "pack_reads", "HIT_DTYPE", "RES_DTYPE"]
+
+
+def _ptr(a) -> int | None:
+    """Address of a numpy array or a torch tensor (None for None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+class Index:
+    """Host FM-index of X and of X reversed (fm_index_build / load)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @classmethod
+    def build(cls, text: np.ndarray, n_seed: int = 0, sa_sample: int = 32, kmer_k: int = 0,
+              threads: int = 0) -> "Index":
+        t = np.ascontiguousarray(text, dtype=np.uint8)
+        opts = _lib.fm_build_opts(n_seed, sa_sample, kmer_k, threads, 0)
+        out = ctypes.c_void_p()
+        check(lib().fm_index_build(_ptr(t), t.size, ctypes.byref(opts), ctypes.byref(out)),
+              "fm_index_build")
+        return cls(out.value)
+
+    @classmethod
+    def load(cls, path: str) -> "Index":
+        out = ctypes.c_void_p()
+        check(lib().fm_index_load(path.encode(), ctypes.byref(out)), "fm_index_load")
+        return cls(out.value)
+
+    def save(self, path: str) -> None:
+        check(lib().fm_index_save(self._h, path.encode()), "fm_index_save")
+
+    def info(self) -> dict:
+        i = _lib.fm_index_info_t()
+        check(lib().fm_index_info(self._h, ctypes.byref(i)), "fm_index_info")
+        return _info_dict(i)
+
+    def to_device(self, device: int = 0, stream=None) -> "DeviceIndex":
+        out = ctypes.c_void_p()
+        check(lib().fm_index_to_device(self._h, device, _stream_ptr(stream), ctypes.byref(out)),
+              "fm_index_to_device")
+        return DeviceIndex(out.value, device)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().fm_index_free(h)
+            self._h = None
+
+
+def _info_dict(i) -> dict:
+    return {"n": i.n, "primary": list(i.primary), "C": [list(i.C[0]), list(i.C[1])],
+            "occ_bytes": i.occ_bytes, "sa_bytes": i.sa_bytes, "kmer_bytes": i.kmer_bytes,
+            "sa_sample": i.sa_sample, "kmer_k": i.kmer_k}
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class DeviceIndex:
+    """Device-resident index image (fm_index_to_device)."""
+
+    def __init__(self, handle: int, device: int):
+        self._h = ctypes.c_void_p(handle)
+        self.device = device
+
+    def info(self) -> dict:
+        i = _lib.fm_index_info_t()
+        check(lib().fm_dindex_info(self._h, ctypes.byref(i)), "fm_dindex_info")
+        return _info_dict(i)
+
+    def search(self, bases, nmask, offsets, lens, z, n_reads: int, params: "Params",
+               res_out, hits_out, stream=None) -> None:
+        """aln_search on device buffers (torch tensors or raw addresses)."""
+        b = _lib.aln_batch(_ptr(bases), _ptr(nmask), _ptr(offsets), _ptr(lens), _ptr(z))
+        r = _lib.aln_result(_ptr(res_out), _ptr(hits_out))
+        p = params.c()
+        check(lib().aln_search(self._h, ctypes.byref(b), n_reads, ctypes.byref(p), ctypes.byref(r),
+                               _stream_ptr(stream)), "aln_search")
+
+    def sa_to_pos(self, hits, n_hits: int, max_width: int, pos_out, npos_out, stream=None) -> None:
+        check(lib().sa_to_pos(self._h, _ptr(hits), n_hits, max_width, _ptr(pos_out), _ptr(npos_out),
+                              _stream_ptr(stream)), "sa_to_pos")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().fm_dindex_free(h)
+            self._h = None
+
+
+@dataclasses.dataclass
+class Params:
+    """Search limits (aln_params)."""
+    z: int = 2
+    max_gapo: int = 1
+    max_gape: int = 2
+    seed_len: int = 0
+    seed_z: int = 0
+    indel_end_skip: int = 5
+    hit_cap: int = 32
+    mode: int = MODE_PLAIN
+    strata: int = STRATA_BEST1
+    work_limit: int = 0
+
+    def c(self) -> _lib.aln_params:
+        return _lib.aln_params(self.z, self.max_gapo, self.max_gape, self.seed_len, self.seed_z,
+                               self.indel_end_skip, self.hit_cap, self.mode, self.strata,
+                               (ctypes.c_uint8 * 3)(), self.work_limit)
+
+    @classmethod
+    def from_limits(cls, lim: dict, **kw) -> "Params":
+        return cls(z=lim["z"], max_gapo=lim["max_gapo"], max_gape=lim["max_gape"],
+                   seed_len=lim["seed_len"], seed_z=lim["seed_z"],
+                   indel_end_skip=lim["indel_end_skip"], **kw)
+
+
+def pack_reads(codes: np.ndarray, offsets: np.ndarray, lens: np.ndarray):
+    """aln_pack_reads: codes 0..4 -> (bases u32, nmask u32, offsets u64), host arrays."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    lens = np.ascontiguousarray(lens, dtype=np.uint16)
+    total = int(lens.astype(np.int64).sum())
+    bases = np.zeros(max(1, (total + 15) // 16), np.uint32)
+    nmask = np.zeros(max(1, (total + 31) // 32), np.uint32)
+    offs = np.zeros(lens.size, np.uint64)
+    check(lib().aln_pack_reads(_ptr(codes), _ptr(offsets), _ptr(lens), lens.size, _ptr(bases),
+                               _ptr(nmask), _ptr(offs)), "aln_pack_reads")
+    return bases, nmask, offs
+
+
+class Aligner:
+    """Device buffers (torch) around a DeviceIndex for host-array convenience calls."""
+
+    def __init__(self, dindex: DeviceIndex):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Aligner needs a CUDA device; there is no CPU path")
+        self.dix = dindex
+        self.torch = torch
+        self.dev = torch.device("cuda", dindex.device)
+
+    def upload(self, codes, offsets, lens, z=None):
+        """Pack reads on the host and copy them to the device."""
+        t = self.torch
+        bases, nmask, offs = pack_reads(codes, offsets, lens)
+        d = {
+            "bases": t.from_numpy(bases.view(np.int32)).to(self.dev),
+            "nmask": t.from_numpy(nmask.view(np.int32)).to(self.dev),
+            "offsets": t.from_numpy(offs.view(np.int64)).to(self.dev),
+            "lens": t.from_numpy(np.ascontiguousarray(lens, np.uint16).view(np.int16)).to(self.dev),
+            "z": None if z is None else t.from_numpy(np.ascontiguousarray(z, np.uint8)).to(self.dev),
+            "n": int(np.asarray(lens).size),
+        }
+        return d
+
+    def outputs(self, n: int, hit_cap: int):
+        t = self.torch
+        res = t.empty(max(1, n) * RES_DTYPE.itemsize, dtype=t.uint8, device=self.dev)
+        hits = t.empty(max(1, n * hit_cap) * HIT_DTYPE.itemsize, dtype=t.uint8, device=self.dev)
+        return res, hits
+
+    def search_device(self, d, params: Params, res, hits, stream=None):
+        self.dix.search(d["bases"], d["nmask"], d["offsets"], d["lens"], d["z"], d["n"], params,
+                        res, hits, stream)
+
+    def align(self, codes, offsets, lens, params: Params, z=None, stream=None):
+        """Host arrays in, numpy (res[n], hits[n, hit_cap]) out."""
+        d = self.upload(codes, offsets, lens, z)
+        n = d["n"]
+        res, hits = self.outputs(n, params.hit_cap)
+        self.search_device(d, params, res, hits, stream)
+        self.torch.cuda.synchronize(self.dev)
+        r = res.cpu().numpy().view(RES_DTYPE)[:n]
+        h = hits.cpu().numpy().view(HIT_DTYPE)[:n * params.hit_cap].reshape(n, params.hit_cap)
+        return r, h
+
+    def positions(self, hits_np: np.ndarray, max_width: int = 16, stream=None):
+        """sa_to_pos for a host array of hits; returns (pos[n, max_width], npos[n])."""
+        t = self.torch
+        h = np.ascontiguousarray(hits_np, dtype=HIT_DTYPE).reshape(-1)
+        n = h.size
+        dh = t.from_numpy(h.view(np.uint8)).to(self.dev)
+        pos = t.zeros(max(1, n * max_width), dtype=t.int64, device=self.dev)
+        npos = t.zeros(max(1, n), dtype=t.int32, device=self.dev)
+        self.dix.sa_to_pos(dh, n, max_width, pos, npos, stream)
+        t.cuda.synchronize(self.dev)
+        return (pos.cpu().numpy().view(np.uint64)[:n * max_width].reshape(n, max_width),
+                npos.cpu().numpy().view(np.uint32)[:n])

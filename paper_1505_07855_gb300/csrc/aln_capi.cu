@@ -1,0 +1,228 @@
+// C ABI: device index image, search dispatch and the SA-to-position walk.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstring>
+#include <string>
+
+#include "aln_device.cuh"
+#include "aln_internal.h"
+#include "aln_search.cuh"
+
+namespace aln {
+cudaError_t launch_search(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
+                          aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, cudaStream_t st);
+}
+
+using namespace aln;
+
+static constexpr int kQueueSlots = 1024;
+
+struct fm_dindex {
+    int device = 0;
+    DIndex X{};
+    fm_index_info_t info{};
+    void *mem[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    uint32_t *queues = nullptr;           // persistent-mode queue counters
+    std::atomic<uint32_t> next_queue{0};
+};
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? ALN_ENOMEM : ALN_EDEVICE,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" void fm_dindex_free(fm_dindex *d) {
+    if (!d) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(d->device);
+    for (auto &row : d->mem)
+        for (void *p : row)
+            if (p) cudaFree(p);
+    if (d->queues) cudaFree(d->queues);
+    cudaSetDevice(prev);
+    delete d;
+}
+
+extern "C" int fm_index_to_device(const fm_index *idx, int device, void *stream, fm_dindex **out) {
+    if (!idx || !out) return fail(ALN_EINVAL, "fm_index_to_device: null argument");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "fm_index_to_device: no CUDA device");
+    if (device < 0 || device >= ndev) return fail(ALN_EINVAL, "fm_index_to_device: bad device ordinal");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "fm_index_to_device: cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fm_dindex *d = new fm_dindex();
+    d->device = device;
+    fm_index_info(idx, &d->info);
+    d->X.kmer_k = idx->kmer_k;
+    uint32_t sh = 0;
+    while ((1u << sh) < idx->sa_sample) sh++;
+    d->X.sa_shift = sh;
+    int rc = ALN_OK;
+    for (int w = 0; w < 2 && rc == ALN_OK; w++) {
+        const HostText &T = idx->t[w];
+        const void *src[3] = {T.blocks.data(), T.sa_samp.data(), T.kmer.data()};
+        const size_t bytes[3] = {T.blocks.size() * 4, T.sa_samp.size() * 4, T.kmer.size() * 4};
+        for (int a = 0; a < 3 && rc == ALN_OK; a++) {
+            if (!bytes[a]) continue;
+            if ((e = cudaMalloc(&d->mem[w][a], bytes[a])) != cudaSuccess) rc = cuda_fail(e, "fm_index_to_device: cudaMalloc");
+            else if ((e = cudaMemcpyAsync(d->mem[w][a], src[a], bytes[a], cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                rc = cuda_fail(e, "fm_index_to_device: copy");
+        }
+        DText &D = d->X.t[w];
+        D.blocks = static_cast<const uint4 *>(d->mem[w][0]);
+        D.sa_samp = static_cast<const uint32_t *>(d->mem[w][1]);
+        D.kmer = static_cast<const uint2 *>(d->mem[w][2]);
+        for (int c = 0; c < 4; c++) D.C1[c] = static_cast<uint32_t>(T.C[c] + 1);
+        D.C1[4] = static_cast<uint32_t>(T.n + 1);
+        D.primary = static_cast<uint32_t>(T.primary);
+        D.n = static_cast<uint32_t>(T.n);
+    }
+    if (rc == ALN_OK) {
+        if ((e = cudaMalloc(&d->queues, kQueueSlots * sizeof(uint32_t))) != cudaSuccess)
+            rc = cuda_fail(e, "fm_index_to_device: cudaMalloc");
+        else if ((e = cudaMemsetAsync(d->queues, 0, kQueueSlots * sizeof(uint32_t), st)) != cudaSuccess)
+            rc = cuda_fail(e, "fm_index_to_device: memset");
+    }
+    if (rc == ALN_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "fm_index_to_device: sync");
+    cudaSetDevice(prev);
+    if (rc != ALN_OK) {
+        fm_dindex_free(d);
+        return rc;
+    }
+    *out = d;
+    return ALN_OK;
+}
+
+extern "C" int fm_dindex_info(const fm_dindex *d, fm_index_info_t *info) {
+    if (!d || !info) return fail(ALN_EINVAL, "fm_dindex_info: null argument");
+    *info = d->info;
+    return ALN_OK;
+}
+
+extern "C" int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads, const aln_params *params,
+                          aln_result *out, void *stream) {
+    if (!idx || !batch || !params || !out) return fail(ALN_EINVAL, "aln_search: null argument");
+    if (n_reads && (!batch->bases || !batch->offset || !batch->len || !out->reads || !out->hits))
+        return fail(ALN_EINVAL, "aln_search: null batch or result array");
+    const aln_params &P = *params;
+    if (P.z > ALN_MAX_Z) return fail(ALN_EINVAL, "aln_search: z > ALN_MAX_Z");
+    if (P.hit_cap < 1) return fail(ALN_EINVAL, "aln_search: hit_cap must be >= 1");
+    if (P.mode > ALN_MODE_PERSISTENT || P.strata > ALN_STRATA_FULL) return fail(ALN_EINVAL, "aln_search: bad mode or strata");
+    SearchParams sp;
+    sp.z = P.z;
+    sp.max_gapo = P.max_gapo;
+    sp.max_gape = P.max_gape;
+    sp.seed_len = P.seed_len;
+    sp.seed_z = P.seed_z;
+    sp.e = P.indel_end_skip;
+    sp.hit_cap = P.hit_cap;
+    sp.strata = P.strata;
+    sp.work_limit = P.work_limit ? P.work_limit : kDefaultWorkLimit;
+    ReadBatch rb{batch->bases, batch->nmask, batch->offset, batch->len, batch->z};
+    fm_dindex *d = const_cast<fm_dindex *>(idx);
+    uint32_t *queue = d->queues + (d->next_queue.fetch_add(1) % kQueueSlots);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != idx->device) cudaSetDevice(idx->device);
+    cudaError_t e = launch_search(idx->X, rb, n_reads, sp, out->reads, out->hits, P.mode, queue,
+                                  static_cast<cudaStream_t>(stream));
+    if (prev != idx->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "aln_search: launch");
+    return ALN_OK;
+}
+
+// ---------------------------------------------------------------- sa_to_pos
+
+namespace aln {
+
+// One thread per (hit, row slot): SA value of row k + j by an LF walk to the
+// nearest sampled row, then the forward-strand start of the target.
+__global__ void sa_walk_kernel(DIndex X, const aln_hit *hits, uint32_t n_hits, uint32_t max_width,
+                               uint64_t *pos_out, uint32_t *n_pos_out) {
+    const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+    const uint64_t h = tid / max_width;
+    const uint32_t j = static_cast<uint32_t>(tid % max_width);
+    if (h >= n_hits) return;
+    const aln_hit H = hits[h];
+    const uint64_t width = static_cast<uint64_t>(H.l) - H.k + 1;
+    if (H.l < H.k || width > max_width || j >= width) return;
+    const DText &T = X.t[H.strand ? 0 : 1];
+    const uint32_t mask = (1u << X.sa_shift) - 1u;
+    const uint32_t limit = 64u << X.sa_shift;
+    uint32_t row = H.k + j, steps = 0;
+    uint64_t sa;
+    bool ok = true;
+    for (;;) {
+        if ((row & mask) == 0) {
+            sa = static_cast<uint64_t>(T.sa_samp[row >> X.sa_shift]) + steps;
+            break;
+        }
+        if (row == T.primary) {  // SA[primary] = 0
+            sa = steps;
+            break;
+        }
+        if (steps >= limit) {
+            ok = false;
+            sa = 0;
+            break;
+        }
+        row = lf_row(T, row);
+        steps++;
+    }
+    uint64_t p = H.strand ? sa : static_cast<uint64_t>(T.n) - sa - H.aligned_len;
+    pos_out[h * max_width + j] = ok ? p : ~0ull;
+    if (!ok) n_pos_out[h] = ALN_POS_WALK_LIMIT;  // racing writers store the same value
+}
+
+// One thread per hit: width flag and ascending order of its positions.
+__global__ void sa_sort_kernel(const aln_hit *hits, uint32_t n_hits, uint32_t max_width, uint64_t *pos_out,
+                               uint32_t *n_pos_out) {
+    const uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= n_hits) return;
+    const aln_hit H = hits[h];
+    const uint64_t width = static_cast<uint64_t>(H.l) - H.k + 1;
+    if (H.l < H.k || width > max_width) {
+        n_pos_out[h] = ALN_POS_TOO_WIDE;
+        return;
+    }
+    if (n_pos_out[h] == ALN_POS_WALK_LIMIT) return;
+    uint64_t *p = pos_out + static_cast<uint64_t>(h) * max_width;
+    for (uint32_t a = 1; a < width; a++) {  // insertion sort, width <= 64
+        uint64_t v = p[a];
+        uint32_t b = a;
+        while (b > 0 && p[b - 1] > v) {
+            p[b] = p[b - 1];
+            b--;
+        }
+        p[b] = v;
+    }
+    n_pos_out[h] = static_cast<uint32_t>(width);
+}
+
+}  // namespace aln
+
+extern "C" int sa_to_pos(const fm_dindex *idx, const aln_hit *hits, uint32_t n_hits, uint32_t max_width,
+                         uint64_t *pos_out, uint32_t *n_pos_out, void *stream) {
+    if (!idx || (n_hits && (!hits || !pos_out || !n_pos_out))) return fail(ALN_EINVAL, "sa_to_pos: null argument");
+    if (max_width < 1 || max_width > 64) return fail(ALN_EINVAL, "sa_to_pos: max_width must be 1..64");
+    if (!n_hits) return ALN_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != idx->device) cudaSetDevice(idx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(n_pos_out, 0, n_hits * sizeof(uint32_t), st);
+    const uint64_t threads = static_cast<uint64_t>(n_hits) * max_width;
+    sa_walk_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(idx->X, hits, n_hits, max_width,
+                                                                                 pos_out, n_pos_out);
+    sa_sort_kernel<<<(n_hits + 255) / 256, 256, 0, st>>>(hits, n_hits, max_width, pos_out, n_pos_out);
+    cudaError_t e = cudaGetLastError();
+    if (prev != idx->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "sa_to_pos: launch");
+    return ALN_OK;
+}

@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA search and SA walk against the oracle, bit-exact, through
+the C ABI (the Python binding passes device pointers to libaln_gb300.so)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1505_07855_gb300 as aln
+from parity_util import compare, oracle_align
+from synth import Rng, Reads, reference_iid, simulate_reads, workload, z_for_length
+
+pytestmark = pytest.mark.gpu
+
+MODES = [aln.MODE_PLAIN, aln.MODE_PERSISTENT]
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+class Pair:
+    """Product index on the device and the oracle's own index of the same text."""
+
+    def __init__(self, text, kmer_k=0, n_seed=0):
+        self.text = text
+        self.ox = oracle.OracleIndex(text, n_seed=n_seed)
+        self.hix = aln.Index.build(text, n_seed=n_seed, kmer_k=kmer_k)
+        self.dix = self.hix.to_device(0)
+        self.al = aln.Aligner(self.dix)
+
+
+@pytest.fixture(scope="module")
+def tiny36(cuda):
+    w = workload("tiny36")
+    return w, Pair(w.text)
+
+
+def _run(pair, reads, lim, hit_cap=32, strata=aln.STRATA_BEST1, mode=aln.MODE_PLAIN, z=None, zmax=None):
+    p = aln.Params.from_limits(lim, hit_cap=hit_cap, strata=strata, mode=mode)
+    if zmax is not None:
+        p.z = zmax
+    return pair.al.align(reads.codes, reads.offsets, reads.lens, p, z=z)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("strata", [aln.STRATA_BEST1, aln.STRATA_FULL])
+def test_tiny36_full_parity(tiny36, mode, strata):
+    """1 Mbp i.i.d. text, 10 000 x 36 bp reads, z=2: every read bit-exact."""
+    w, pair = tiny36
+    rg, hg = _run(pair, w.reads, w.params, strata=strata, mode=mode)
+    ro, ho, _ = oracle_align(pair.ox, w.reads, w.params, 32, strata)
+    assert compare(rg, hg, ro, ho, what="tiny36") == 10_000
+    assert (rg["n_hits"] > 0).mean() > 0.95
+
+
+def test_hand_example(cuda):
+    enc = {c: i for i, c in enumerate("ACGT")}
+    X = np.array([enc[c] for c in "ACGTTACGAT"], np.uint8)
+    pair = Pair(X)
+    W = np.array([enc[c] for c in "ACGA"], np.uint8)
+    reads = Reads(W, np.zeros(1, np.uint64), np.array([4], np.uint16), np.array([1], np.uint8),
+                  np.zeros(1, np.int64), np.zeros(1, np.uint8))
+    lim = dict(z=1, max_gapo=0, max_gape=0, seed_len=0, seed_z=0, indel_end_skip=5)
+    rg, hg = _run(pair, reads, lim, hit_cap=8, strata=aln.STRATA_FULL)
+    assert rg[0]["n_hits"] == 3 and (rg[0]["d_best"], rg[0]["c0"], rg[0]["c1"]) == (0, 1, 2)
+    assert [(int(h["strand"]), int(h["k"]), int(h["l"])) for h in hg[0, :3]] == [(0, 2, 2), (0, 9, 9), (1, 2, 2)]
+    pos, npos = pair.al.positions(hg[0, :3], 16)
+    assert npos.tolist() == [1, 1, 1] and pos[:, 0].tolist() == [5, 0, 0]
+
+
+LIMITS = [
+    dict(z=1, max_gapo=0, max_gape=0, seed_len=0, seed_z=0, indel_end_skip=5),
+    dict(z=2, max_gapo=1, max_gape=2, seed_len=0, seed_z=0, indel_end_skip=5),
+    dict(z=3, max_gapo=2, max_gape=1, seed_len=0, seed_z=0, indel_end_skip=0),
+    dict(z=3, max_gapo=1, max_gape=3, seed_len=12, seed_z=1, indel_end_skip=3),
+    dict(z=4, max_gapo=1, max_gape=6, seed_len=32, seed_z=2, indel_end_skip=5),
+    dict(z=5, max_gapo=1, max_gape=2, seed_len=0, seed_z=0, indel_end_skip=5),
+    dict(z=7, max_gapo=2, max_gape=3, seed_len=8, seed_z=3, indel_end_skip=1),
+]
+
+
+@pytest.mark.parametrize("li", range(len(LIMITS)))
+@pytest.mark.parametrize("strata", [aln.STRATA_BEST1, aln.STRATA_FULL])
+def test_limits_parity(cuda, li, strata):
+    """Small texts (several Occ blocks, ragged tails), reads with errors and N,
+    across gap / seed / end-window / z settings and both strata."""
+    lim = LIMITS[li]
+    rng = Rng(1000 + li, "lim")
+    text = reference_iid(20_000 + 37 * li, rng.sub("t"))
+    pair = Pair(text)
+    m = [20, 36, 50, 36, 60, 76, 40][li]
+    reads = simulate_reads(text, 600, m, rng.sub("r"), sub_rate=(0.02, 0.04), indel_rate=0.005,
+                           indel_lens=(1, 2), n_frac=0.1, z=lim["z"])
+    for mode in MODES:
+        rg, hg = _run(pair, reads, lim, hit_cap=40, strata=strata, mode=mode)
+        ro, ho, _ = oracle_align(pair.ox, reads, lim, 40, strata)
+        compare(rg, hg, ro, ho, what=f"limits {li} mode {mode}")
+
+
+def test_mixed_lengths_per_read_z(cuda):
+    """Reads of 36..250 bp mixed in one batch with z = min(6, ceil(0.04 len)),
+    repeats and N runs in the text (the mixed-length recipe at small scale)."""
+    w = workload("human_mixed", ref_len=3_000_000, n_reads=3000, seed=3)
+    pair = Pair(w.text, n_seed=7)
+    lim = w.params
+    for mode in MODES:
+        rg, hg = _run(pair, w.reads, lim, hit_cap=32, mode=mode, z=w.reads.z, zmax=6)
+        ro, ho, _ = oracle_align(pair.ox, w.reads, lim, 32, oracle.BEST1, z=w.reads.z)
+        compare(rg, hg, ro, ho, what=f"mixed mode {mode}")
+
+
+def test_chr100_scaled_parity(cuda):
+    """The 100 bp Markov + repeat-family recipe at 4 Mbp, every read."""
+    w = workload("chr100", ref_len=4_000_000, n_reads=4000, seed=1)
+    pair = Pair(w.text)
+    for mode in MODES:
+        rg, hg = _run(pair, w.reads, w.params, mode=mode)
+        ro, ho, _ = oracle_align(pair.ox, w.reads, w.params, 32, oracle.BEST1)
+        compare(rg, hg, ro, ho, what=f"chr100-4M mode {mode}")
+
+
+def test_edge_cases(cuda):
+    text = reference_iid(5000, Rng(7, "edge"))
+    pair = Pair(text)
+    parts = [np.zeros(0, np.uint8), text[10:11], np.full(12, 4, np.uint8), np.zeros(256, np.uint8),
+             text[100:355], text[4000:4036], text[4964:5000], text[0:36]]
+    lens = np.array([p.size for p in parts], np.uint16)
+    offs = np.zeros(lens.size, np.uint64)
+    offs[1:] = np.cumsum(lens[:-1].astype(np.uint64))
+    z = np.array([2, 0, 2, 2, 6, 7, 2, 2], np.uint8)
+    reads = Reads(np.concatenate(parts), offs, lens, z, np.zeros(lens.size, np.int64),
+                  np.zeros(lens.size, np.uint8))
+    lim = dict(z=7, max_gapo=1, max_gape=2, seed_len=0, seed_z=0, indel_end_skip=5)
+    for cap in (1, 4):
+        rg, hg = _run(pair, reads, lim, hit_cap=cap, z=z, zmax=6)
+        ro, ho, _ = oracle_align(pair.ox, reads, lim, cap, oracle.BEST1, z=z)
+        # z=7 > params.z=6 is flagged by the GPU (declared bound), not by the oracle
+        assert rg[5]["flags"] & aln.FLAG_BAD_LIMIT and rg[5]["n_hits"] == 0
+        keep = np.array([i for i in range(lens.size) if i != 5])
+        compare(rg[keep], hg[keep], ro[keep], ho[keep], idx=keep, what=f"edge cap {cap}")
+        assert rg[3]["flags"] & aln.FLAG_READ_TOO_LONG
+        assert rg[0]["n_hits"] == 0 and rg[0]["d_best"] == 255
+
+
+def test_unaligned_offsets_and_order(cuda, tiny36):
+    """Reads shuffled and duplicated (36 bp reads packed back to back start at
+    base offsets that are not word aligned): each read's result is unchanged."""
+    w, pair = tiny36
+    sub = w.reads.subset(np.arange(500))
+    rng = np.random.default_rng(3)
+    perm = np.concatenate([rng.permutation(500), rng.integers(0, 500, 100)])
+    shuffled = sub.subset(perm)
+    p = aln.Params.from_limits(w.params, hit_cap=32)
+    r1, h1 = pair.al.align(sub.codes, sub.offsets, sub.lens, p)
+    r2, h2 = pair.al.align(shuffled.codes, shuffled.offsets, shuffled.lens, p)
+    assert np.array_equal(r2, r1[perm])
+    valid = np.arange(32)[None, :] < r2["n_hits"][:, None]
+    for f in ("k", "l", "aligned_len", "strand", "n_diff", "n_mm", "n_gapo", "n_gape"):
+        assert np.array_equal(np.where(valid, h2[f], 0), np.where(valid, h1[perm][f], 0))
+
+
+def test_sa_to_pos_parity(cuda, tiny36):
+    w, pair = tiny36
+    rg, hg = _run(pair, w.reads.subset(np.arange(3000)), w.params, strata=aln.STRATA_FULL)
+    hits = np.concatenate([hg[i, :rg[i]["n_hits"]] for i in range(rg.size)])
+    pos, npos = pair.al.positions(hits, 16)
+    ohits = np.zeros(hits.size, oracle.HIT_DTYPE)
+    for f in ("k", "l", "aligned_len", "strand"):
+        ohits[f] = hits[f]
+    opos, onpos = pair.ox.positions(ohits, 16)
+    width = hits["l"].astype(np.int64) - hits["k"] + 1
+    wide = width > 16
+    assert (npos[wide] == aln.POS_TOO_WIDE).all()
+    assert np.array_equal(npos[~wide], onpos[~wide])
+    for i in np.nonzero(~wide)[0]:
+        assert np.array_equal(pos[i, :npos[i]], opos[i, :npos[i]])
+    # every position is where the target starts: the forward read's true origin
+    # is among the positions of its best forward hit for error-free reads
+    assert (~wide).sum() > 2000
+
+
+def test_chr100_full_size_sampled(cuda):
+    """Full size (100 Mbp text, 1 M x 100 bp reads, z=4, seed 32/2) in the launch
+    configurations the benchmark times: every read searched on the GPU, a seeded
+    sample of 3000 reads (plus every read with more than one hit) recomputed by
+    the oracle one by one and compared bit-exact; plain == persistent on all."""
+    w = workload("chr100")
+    pair = Pair(w.text)
+    p = aln.Params.from_limits(w.params, hit_cap=32)
+    rp, hp = pair.al.align(w.reads.codes, w.reads.offsets, w.reads.lens, p)
+    p.mode = aln.MODE_PERSISTENT
+    rq, hq = pair.al.align(w.reads.codes, w.reads.offsets, w.reads.lens, p)
+    assert np.array_equal(rp, rq) and np.array_equal(hp, hq)
+    rng = np.random.default_rng(2024)
+    sample = np.unique(np.concatenate([rng.choice(w.reads.n, 3000, replace=False),
+                                       np.nonzero(rp["n_hits"] > 1)[0][:2000]]))
+    sub = w.reads.subset(sample)
+    ro, ho, _ = oracle_align(pair.ox, sub, w.params, 32, oracle.BEST1)
+    compare(rp[sample], hp[sample], ro, ho, idx=sample, what="chr100 full")
