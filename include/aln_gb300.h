@@ -213,6 +213,35 @@ int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
 int sa_to_pos(const fm_dindex *idx, const aln_hit *hits, uint32_t n_hits, uint32_t max_width,
               uint64_t *pos_out, uint32_t *n_pos_out, void *stream);
 
+/* ---------------------------------------------------------------- no-allocation variant
+ *
+ * The paper has no counterpart to this call; it exists for callers of this
+ * library that cannot call cudaMalloc: for example a process whose device
+ * memory is entirely owned by another allocator (a framework's caching
+ * allocator that reserves the device up front), or a serving loop that must not
+ * allocate after start-up because an allocation can block, synchronise the
+ * device or fail under memory pressure.
+ *
+ * aln_search_noalloc runs the persistent search (params.mode is ignored) exactly
+ * as aln_search does and writes the same results into the caller's buffers.
+ * Its only scratch, the device work-queue counter, lives in a fixed array of
+ * ALN_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that loads
+ * the library holds until the process exits.  The call allocates nothing.
+ *  - The first call on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress) and caches it; make that first call before
+ *    any stream capture on the device.
+ *  - All calls share the one array and it keeps the last call's contents; each
+ *    call clears the counter on its stream before its kernel starts.  Calls that
+ *    overlap on the GPU (different streams, or host threads racing) race on the
+ *    counter and give wrong results: serialise them.
+ *  - n_reads above ALN_NOALLOC_MAX_READS (the counter's range) is rejected with
+ *    ALN_EINVAL and a message; nothing is launched.
+ * Other arguments, errors and the result definition are those of aln_search. */
+#define ALN_NOALLOC_SCRATCH_BYTES 256
+#define ALN_NOALLOC_MAX_READS 0x80000000u
+int aln_search_noalloc(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
+                       const aln_params *params, aln_result *out, void *stream);
+
 /* Host helper: pack reads (codes 0..4, read r at codes[code_offset[r]] of
  * length len[r]) back to back into the aln_batch layout.  bases_out needs
  * ceil(total/16) words, nmask_out ceil(total/32) words (total = sum of len),

@@ -3,6 +3,7 @@
 
 #include <atomic>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "aln_device.cuh"
@@ -225,4 +226,73 @@ extern "C" int sa_to_pos(const fm_dindex *idx, const aln_hit *hits, uint32_t n_h
     if (prev != idx->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(e, "sa_to_pos: launch");
     return ALN_OK;
+}
+
+// ---------------------------------------------------------------- aln_search_noalloc
+//
+// The persistent search with its work-queue counter in a fixed, file-scope
+// device array instead of memory the library allocated.  For callers that
+// cannot call cudaMalloc (see the header).  Host code never dereferences the
+// array's name: on the host it only stands in for the symbol, so its device
+// address is looked up once per device with cudaGetSymbolAddress and that
+// address is what the kernel receives.
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+static __device__ __align__(256) uint32_t g_noalloc_scratch[ALN_NOALLOC_SCRATCH_BYTES / sizeof(uint32_t)];
+std::mutex g_noalloc_mu;
+uint32_t *g_noalloc_ptr[kNoallocMaxDevices] = {};
+}  // namespace
+
+// Device address of the scratch array on the current device (set up on first use).
+static int noalloc_scratch(int device, uint32_t **out) {
+    if (device < 0 || device >= kNoallocMaxDevices)
+        return fail(ALN_EINVAL, "aln_search_noalloc: device ordinal beyond the supported range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "aln_search_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[device] = static_cast<uint32_t *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return ALN_OK;
+}
+
+extern "C" int aln_search_noalloc(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
+                                  const aln_params *params, aln_result *out, void *stream) {
+    if (!idx || !batch || !params || !out) return fail(ALN_EINVAL, "aln_search_noalloc: null argument");
+    if (n_reads > ALN_NOALLOC_MAX_READS)
+        return fail(ALN_EINVAL, "aln_search_noalloc: n_reads exceeds ALN_NOALLOC_MAX_READS (the range of the "
+                                "work-queue counter in the fixed scratch array)");
+    if (n_reads && (!batch->bases || !batch->offset || !batch->len || !out->reads || !out->hits))
+        return fail(ALN_EINVAL, "aln_search_noalloc: null batch or result array");
+    const aln_params &P = *params;
+    if (P.z > ALN_MAX_Z) return fail(ALN_EINVAL, "aln_search_noalloc: z > ALN_MAX_Z");
+    if (P.hit_cap < 1) return fail(ALN_EINVAL, "aln_search_noalloc: hit_cap must be >= 1");
+    if (P.strata > ALN_STRATA_FULL) return fail(ALN_EINVAL, "aln_search_noalloc: bad strata");
+    SearchParams sp;
+    sp.z = P.z;
+    sp.max_gapo = P.max_gapo;
+    sp.max_gape = P.max_gape;
+    sp.seed_len = P.seed_len;
+    sp.seed_z = P.seed_z;
+    sp.e = P.indel_end_skip;
+    sp.hit_cap = P.hit_cap;
+    sp.strata = P.strata;
+    sp.work_limit = P.work_limit ? P.work_limit : kDefaultWorkLimit;
+    ReadBatch rb{batch->bases, batch->nmask, batch->offset, batch->len, batch->z};
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != idx->device) cudaSetDevice(idx->device);
+    uint32_t *scratch = nullptr;
+    int rc = noalloc_scratch(idx->device, &scratch);
+    if (rc == ALN_OK) {
+        // launch_search clears the queue counter (scratch[0]) on the stream first
+        cudaError_t e = launch_search(idx->X, rb, n_reads, sp, out->reads, out->hits, ALN_MODE_PERSISTENT, scratch,
+                                      static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) rc = cuda_fail(e, "aln_search_noalloc: launch");
+    }
+    if (prev != idx->device) cudaSetDevice(prev);
+    return rc;
 }
