@@ -172,6 +172,8 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=dev)
     t_all = time.time()
     w = workload(args.workload)
+    if args.reads:
+        w.reads = w.reads.subset(np.arange(min(args.reads, w.reads.n)))
     lim = w.params
     n = w.reads.n
     # index: rank 0 builds and saves, the other replicas load the image
@@ -198,7 +200,8 @@ def run_gpu(args):
     res, hits = al.outputs(n, hit_cap)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     modes = {"persistent": aln.MODE_PERSISTENT, "plain": aln.MODE_PLAIN}
-    params = {k: aln.Params.from_limits(lim, hit_cap=hit_cap, mode=m) for k, m in modes.items()}
+    params = {k: aln.Params.from_limits(lim, hit_cap=hit_cap, mode=m, blocks_per_sm=args.blocks_per_sm)
+              for k, m in modes.items()}
 
     def step(mode):
         al.search_device(d, params[mode], res, hits, stream)
@@ -336,10 +339,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="chr100", choices=["chr100", "tiny36"])
-    ap.add_argument("--kmer-k", type=int, default=0)
+    ap.add_argument("--kmer-k", type=int, default=10)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=2000)
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--reads", type=int, default=0, help="use only the first N reads (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -55,7 +55,7 @@ extern "C" {
 #define ALN_MAX_READ_LEN 255 /* longer reads get ALN_FLAG_READ_TOO_LONG and no hits */
 #define ALN_MAX_Z 7          /* largest difference limit; larger per-read z is flagged */
 #define ALN_MAX_HIT_CAP 255
-#define ALN_MAX_KMER_K 13
+#define ALN_MAX_KMER_K 12
 #define ALN_CAND_CAP 64      /* distinct candidate hits kept per read by the kernels */
 
 /* ---------------------------------------------------------------- per-read flags */
@@ -81,7 +81,9 @@ typedef struct fm_dindex fm_dindex; /* device-resident index image (opaque) */
 typedef struct {
     uint64_t n_seed;    /* every N of the text is indexed as splitmix64(n_seed ^ pos) & 3 */
     uint32_t sa_sample; /* keep SA[r] for rows r % sa_sample == 0; power of two 1..1024; 0 -> 32 */
-    uint32_t kmer_k;    /* k of the k-mer interval table, 0 = none, <= ALN_MAX_KMER_K */
+    uint32_t kmer_k;    /* interval table of every string of length 1..kmer_k (a prefix
+                           trie), 0 = none, <= ALN_MAX_KMER_K; result-neutral, it replaces
+                           Occ steps of short targets by one table read */
     int32_t n_threads;  /* host threads for construction; 0 = all online cores */
     uint32_t reserved;
 } fm_build_opts;
@@ -92,7 +94,7 @@ typedef struct {
     uint64_t C[2][4];    /* C arrays of X and Xr */
     uint64_t occ_bytes;  /* bytes of Occ blocks per text: 64 per 192 rows */
     uint64_t sa_bytes;   /* bytes of sampled SA per text */
-    uint64_t kmer_bytes; /* bytes of k-mer table per text */
+    uint64_t kmer_bytes; /* bytes of the prefix-trie interval table per text */
     uint32_t sa_sample;
     uint32_t kmer_k;
 } fm_index_info_t;
@@ -105,7 +107,7 @@ int fm_index_build(const uint8_t *text, uint64_t n, const fm_build_opts *opts, f
 void fm_index_free(fm_index *idx);
 int fm_index_info(const fm_index *idx, fm_index_info_t *info);
 
-/* Write / read the index image (little-endian binary, magic "ALNFMIX1").
+/* Write / read the index image (little-endian binary, magic "ALNFMIX3").
  * Load returns ALN_EIO on a missing, short or malformed file. */
 int fm_index_save(const fm_index *idx, const char *path);
 int fm_index_load(const char *path, fm_index **out);
@@ -149,7 +151,10 @@ typedef struct {
     uint8_t hit_cap;        /* hits written per read, 1..ALN_MAX_HIT_CAP */
     uint8_t mode;           /* ALN_MODE_* */
     uint8_t strata;         /* ALN_STRATA_* */
-    uint8_t reserved[3];
+    uint8_t blocks_per_sm;  /* persistent form: resident 128-thread blocks per SM; 0 = as
+                               many as fit.  Fewer lanes give each lane more reads, which
+                               shortens the tail where a warp waits for its slowest read */
+    uint8_t reserved[2];
     uint32_t work_limit;    /* node expansions per read before ALN_FLAG_WORK_LIMIT; 0 = 2^24 */
 } aln_params;
 

@@ -141,11 +141,12 @@ class Params:
     mode: int = MODE_PLAIN
     strata: int = STRATA_BEST1
     work_limit: int = 0
+    blocks_per_sm: int = 0
 
     def c(self) -> _lib.aln_params:
         return _lib.aln_params(self.z, self.max_gapo, self.max_gape, self.seed_len, self.seed_z,
                                self.indel_end_skip, self.hit_cap, self.mode, self.strata,
-                               (ctypes.c_uint8 * 3)(), self.work_limit)
+                               self.blocks_per_sm, (ctypes.c_uint8 * 2)(), self.work_limit)
 
     @classmethod
     def from_limits(cls, lim: dict, **kw) -> "Params":

@@ -61,7 +61,8 @@ class aln_params(ctypes.Structure):
                 ("seed_len", ctypes.c_uint8), ("seed_z", ctypes.c_uint8),
                 ("indel_end_skip", ctypes.c_uint8), ("hit_cap", ctypes.c_uint8),
                 ("mode", ctypes.c_uint8), ("strata", ctypes.c_uint8),
-                ("reserved", ctypes.c_uint8 * 3), ("work_limit", ctypes.c_uint32)]
+                ("blocks_per_sm", ctypes.c_uint8), ("reserved", ctypes.c_uint8 * 2),
+                ("work_limit", ctypes.c_uint32)]
 
 
 class aln_result(ctypes.Structure):

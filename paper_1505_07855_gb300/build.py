@@ -29,8 +29,8 @@ def _newer(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], out_dir: str = BUILD) -> str:
+    obj = os.path.join(out_dir, os.path.basename(src) + ".o")
     deps = [os.path.join(CSRC, src)] + [os.path.join(CSRC, h) for h in HEADERS] + \
         [os.path.join(INCLUDE, "aln_gb300.h")]
     if not _newer(obj, deps):
@@ -46,22 +46,28 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every source for sm_103a and link the library; returns its path."""
-    if force and os.path.isdir(BUILD):
-        shutil.rmtree(BUILD)
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, stats: bool = False, variant: str = "",
+          defines: tuple = ()) -> str:
+    """Compile every source for sm_103a and link the library; returns its path.
+    stats=True builds the instrumented variant (event counters) into _build/stats;
+    variant/defines build a tuning variant into _build/<variant>."""
+    out_dir = os.path.join(BUILD, "stats" if stats else variant) if (stats or variant) else BUILD
+    lib = os.path.join(out_dir, "libaln_gb300.so")
+    if force and os.path.isdir(out_dir):
+        shutil.rmtree(out_dir)
+    os.makedirs(out_dir, exist_ok=True)
     srcs = CU_SOURCES + CPP_SOURCES
+    defs = (["-DALN_STATS"] if stats else []) + [f"-D{d}" for d in defines]
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, ["-Xptxas", "-v"] if verbose and s.endswith(".cu") else []),
-                           srcs))
-    if _newer(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, defs + (["-Xptxas", "-v"] if verbose and s.endswith(".cu") else []),
+                                              out_dir), srcs))
+    if _newer(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                "-Xlinker", "-rpath", "-Xlinker", os.path.join(CUDA_HOME, "lib64"), "-lpthread"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

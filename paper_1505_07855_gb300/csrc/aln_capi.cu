@@ -125,6 +125,7 @@ extern "C" int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t
     sp.hit_cap = P.hit_cap;
     sp.strata = P.strata;
     sp.work_limit = P.work_limit ? P.work_limit : kDefaultWorkLimit;
+    sp.blocks_per_sm = P.blocks_per_sm;
     ReadBatch rb{batch->bases, batch->nmask, batch->offset, batch->len, batch->z};
     fm_dindex *d = const_cast<fm_dindex *>(idx);
     uint32_t *queue = d->queues + (d->next_queue.fetch_add(1) % kQueueSlots);
@@ -281,6 +282,7 @@ extern "C" int aln_search_noalloc(const fm_dindex *idx, const aln_batch *batch, 
     sp.hit_cap = P.hit_cap;
     sp.strata = P.strata;
     sp.work_limit = P.work_limit ? P.work_limit : kDefaultWorkLimit;
+    sp.blocks_per_sm = P.blocks_per_sm;
     ReadBatch rb{batch->bases, batch->nmask, batch->offset, batch->len, batch->z};
     int prev = 0;
     cudaGetDevice(&prev);
@@ -296,3 +298,14 @@ extern "C" int aln_search_noalloc(const fm_dindex *idx, const aln_batch *batch, 
     if (prev != idx->device) cudaSetDevice(prev);
     return rc;
 }
+
+#ifdef ALN_STATS
+namespace aln {
+cudaError_t debug_stats(unsigned long long *out, int reset);
+}
+// Instrumented builds only (not part of the ABI): counters of the persistent kernel.
+extern "C" int aln_debug_stats(unsigned long long *out16, int reset) {
+    cudaError_t e = aln::debug_stats(out16, reset);
+    return e == cudaSuccess ? ALN_OK : cuda_fail(e, "aln_debug_stats");
+}
+#endif

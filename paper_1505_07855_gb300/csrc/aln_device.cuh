@@ -6,6 +6,12 @@
 //     lo' = C1[c] + occ_before(c, lo),  hi' = C1[c] + occ_before(c, hi),
 // with C1[c] = C[c] + 1 and occ_before(c, j) = number of c in B[0 .. j-1].
 // It is empty ("the pointers cross") iff hi' <= lo'.
+//
+// Block layout (64 bytes per 192 rows): cnt[4] = occurrences of A, C, G, T
+// before the block's middle row (192 b + 96), $ and end padding counted as A;
+// then 12 words of 2-bit symbols (A=00 C=01 G=10 T=11), 16 per word.  A row at
+// offset o in the block counts forwards over symbols [96, o) or backwards over
+// [o, 96): at most 6 words, merged two words per popcount.
 #pragma once
 
 #include <cstdint>
@@ -13,6 +19,7 @@
 namespace aln {
 
 constexpr uint32_t kRowsPerBlock = 192;
+constexpr uint32_t kHalfRows = 96;
 
 struct DText {
     const uint4 *blocks;     // 4 x uint4 per 64-byte block: counts, then 12 symbol words
@@ -51,63 +58,44 @@ __device__ __forceinline__ void load_block(const uint4 *blocks, uint32_t b, Bloc
     B.w[8] = q3.x; B.w[9] = q3.y; B.w[10] = q3.z; B.w[11] = q3.w;
 }
 
-// Counts of A, C, G, T among the first r (0..191) symbols of a block.
-// Symbol bits (hi, lo): A=00 C=01 G=10 T=11.
-__device__ __forceinline__ void count4_prefix(const Block &B, uint32_t r, uint32_t out[4]) {
-    const uint32_t full = r >> 4, rem = r & 15u;
+// Mask of the low k symbols (k = 0..16) of a word, lo bit of each symbol only.
+__device__ __forceinline__ uint32_t sym_mask(int k) {
+    k = k < 0 ? 0 : (k > 16 ? 16 : k);
+    return __funnelshift_lc(0xFFFFFFFFu, 0u, 2u * static_cast<uint32_t>(k)) & 0x55555555u;
+}
+
+// occ_before(c, 192 b + o) for all four bases (before the $ correction).
+__device__ __forceinline__ void occ4_in_block(const Block &B, uint32_t o, uint32_t occ[4]) {
+    const bool up = o >= kHalfRows;
+    const int x = static_cast<int>(up ? o - kHalfRows : o);
     uint32_t nlo = 0, nhi = 0, nboth = 0;
 #pragma unroll
-    for (uint32_t t = 0; t < 12; t++) {
-        uint32_t m = (t < full) ? 0x55555555u : ((t == full) ? (((1u << (2 * rem)) - 1u) & 0x55555555u) : 0u);
-        uint32_t lo = B.w[t] & m, hi = (B.w[t] >> 1) & m;
-        nlo += __popc(lo);
-        nhi += __popc(hi);
-        nboth += __popc(lo & hi);
+    for (int pr = 0; pr < 3; pr++) {
+        const uint32_t wa = up ? B.w[6 + 2 * pr] : B.w[2 * pr];
+        const uint32_t wb = up ? B.w[7 + 2 * pr] : B.w[2 * pr + 1];
+        uint32_t ma = sym_mask(x - 32 * pr), mb = sym_mask(x - 32 * pr - 16);
+        if (!up) {  // backwards: symbols at or after o
+            ma ^= 0x55555555u;
+            mb ^= 0x55555555u;
+        }
+        const uint32_t la = wa & ma, ha = (wa >> 1) & ma;
+        const uint32_t lb = wb & mb, hb = (wb >> 1) & mb;
+        nlo += __popc(la | (lb << 1));
+        nhi += __popc(ha | (hb << 1));
+        nboth += __popc((la & ha) | ((lb & hb) << 1));
     }
-    out[3] = nboth;
-    out[2] = nhi - nboth;
-    out[1] = nlo - nboth;
-    out[0] = r - out[1] - out[2] - out[3];
-}
-
-// Count of symbol c among the first r symbols of a block.
-__device__ __forceinline__ uint32_t count1_prefix(const Block &B, uint32_t r, uint32_t c) {
-    const uint32_t full = r >> 4, rem = r & 15u;
-    const uint32_t pat = c * 0x55555555u;  // c replicated in every 2-bit lane
-    uint32_t n = 0;
-#pragma unroll
-    for (uint32_t t = 0; t < 12; t++) {
-        uint32_t m = (t < full) ? 0x55555555u : ((t == full) ? (((1u << (2 * rem)) - 1u) & 0x55555555u) : 0u);
-        uint32_t x = B.w[t] ^ pat;
-        n += __popc(~(x | (x >> 1)) & m);
-    }
-    return n;
-}
-
-// occ_before for all four symbols at rows lo and hi (one or two block reads).
-__device__ __forceinline__ void occ4_pair(const DText &T, uint32_t lo, uint32_t hi, uint32_t olo[4],
-                                          uint32_t ohi[4]) {
-    const uint32_t blo = lo / kRowsPerBlock, bhi = hi / kRowsPerBlock;
-    Block Bl, Bh;
-    load_block(T.blocks, blo, Bl);
-    if (bhi != blo) load_block(T.blocks, bhi, Bh);
-    count4_prefix(Bl, lo - blo * kRowsPerBlock, olo);
-    if (bhi != blo) {
-        count4_prefix(Bh, hi - bhi * kRowsPerBlock, ohi);
-#pragma unroll
-        for (int c = 0; c < 4; c++) ohi[c] += Bh.cnt[c];
+    const uint32_t nsym = up ? static_cast<uint32_t>(x) : kHalfRows - static_cast<uint32_t>(x);
+    const uint32_t cT = nboth, cG = nhi - nboth, cC = nlo - nboth;
+    const uint32_t cA = nsym - cT - cG - cC;
+    if (up) {
+        occ[0] = B.cnt[0] + cA; occ[1] = B.cnt[1] + cC; occ[2] = B.cnt[2] + cG; occ[3] = B.cnt[3] + cT;
     } else {
-        count4_prefix(Bl, hi - blo * kRowsPerBlock, ohi);
-#pragma unroll
-        for (int c = 0; c < 4; c++) ohi[c] += Bl.cnt[c];
+        occ[0] = B.cnt[0] - cA; occ[1] = B.cnt[1] - cC; occ[2] = B.cnt[2] - cG; occ[3] = B.cnt[3] - cT;
     }
-#pragma unroll
-    for (int c = 0; c < 4; c++) olo[c] += Bl.cnt[c];
-    olo[0] -= (lo > T.primary) ? 1u : 0u;
-    ohi[0] -= (hi > T.primary) ? 1u : 0u;
 }
 
-// Extend [lo, hi) by every base: children (lo4[c], hi4[c]).
+// Extend [lo, hi) by every base: children (lo4[c], hi4[c]).  Both block reads
+// are issued before either is used; a second read of the same block is skipped.
 __device__ __forceinline__ void lf4(const DText &T, uint32_t lo, uint32_t hi, uint32_t lo4[4], uint32_t hi4[4]) {
     if (lo == 0 && hi == T.n + 1) {  // the empty string: children are the C ranges
 #pragma unroll
@@ -117,8 +105,16 @@ __device__ __forceinline__ void lf4(const DText &T, uint32_t lo, uint32_t hi, ui
         }
         return;
     }
+    const uint32_t blo = lo / kRowsPerBlock, bhi = hi / kRowsPerBlock;
+    Block Bl, Bh;
+    load_block(T.blocks, blo, Bl);
+    if (bhi != blo) load_block(T.blocks, bhi, Bh);
+    else Bh = Bl;
     uint32_t olo[4], ohi[4];
-    occ4_pair(T, lo, hi, olo, ohi);
+    occ4_in_block(Bl, lo - blo * kRowsPerBlock, olo);
+    occ4_in_block(Bh, hi - bhi * kRowsPerBlock, ohi);
+    olo[0] -= (lo > T.primary) ? 1u : 0u;
+    ohi[0] -= (hi > T.primary) ? 1u : 0u;
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         lo4[c] = T.C1[c] + olo[c];
@@ -128,34 +124,22 @@ __device__ __forceinline__ void lf4(const DText &T, uint32_t lo, uint32_t hi, ui
 
 // Extend [lo, hi) by base c.
 __device__ __forceinline__ void lf1(const DText &T, uint32_t c, uint32_t &lo, uint32_t &hi) {
-    if (lo == 0 && hi == T.n + 1) {
-        lo = T.C1[c];
-        hi = T.C1[c + 1];
-        return;
-    }
-    const uint32_t blo = lo / kRowsPerBlock, bhi = hi / kRowsPerBlock;
-    Block Bl, Bh;
-    load_block(T.blocks, blo, Bl);
-    if (bhi != blo) load_block(T.blocks, bhi, Bh);
-    uint32_t a = Bl.cnt[c] + count1_prefix(Bl, lo - blo * kRowsPerBlock, c);
-    uint32_t b = (bhi != blo) ? Bh.cnt[c] + count1_prefix(Bh, hi - bhi * kRowsPerBlock, c)
-                              : Bl.cnt[c] + count1_prefix(Bl, hi - blo * kRowsPerBlock, c);
-    if (c == 0) {
-        a -= (lo > T.primary) ? 1u : 0u;
-        b -= (hi > T.primary) ? 1u : 0u;
-    }
-    lo = T.C1[c] + a;
-    hi = T.C1[c] + b;
+    uint32_t lo4[4], hi4[4];
+    lf4(T, lo, hi, lo4, hi4);
+    lo = lo4[c];
+    hi = hi4[c];
 }
 
-// BWT symbol at row r (r != primary) and occ_before of it at r: one LF step of
-// the row itself, LF(r) = C1[B[r]] + occ_before(B[r], r).
+// LF(r) = C1[B[r]] + occ_before(B[r], r) for a row r != primary: the row of the
+// suffix that starts one text position earlier.
 __device__ __forceinline__ uint32_t lf_row(const DText &T, uint32_t r) {
     const uint32_t b = r / kRowsPerBlock, o = r - b * kRowsPerBlock;
     Block B;
     load_block(T.blocks, b, B);
     const uint32_t c = (B.w[o >> 4] >> (2 * (o & 15u))) & 3u;
-    uint32_t v = B.cnt[c] + count1_prefix(B, o, c);
+    uint32_t occ[4];
+    occ4_in_block(B, o, occ);
+    uint32_t v = occ[c];
     if (c == 0) v -= (r > T.primary) ? 1u : 0u;
     return T.C1[c] + v;
 }

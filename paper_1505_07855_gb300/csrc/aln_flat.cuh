@@ -1,0 +1,555 @@
+// Persistent search as one flat per-lane state machine (sm_103a).
+//
+// Every iteration of the kernel's single loop has three parts:
+//   control  -- cheap, divergent: the lane advances its own read (take the next
+//               read from the device queue, load it, step the D scan, pop the
+//               stack, emit a hit, finish a strand or a pass, reduce and write
+//               the result) until it needs the four extensions of one interval;
+//   fetch    -- the four extensions, from one of two sources: a 32-byte group
+//               of the prefix-trie table when the node's target is shorter than
+//               k (the interval of a string depends on the string alone), else
+//               the Occ blocks at the two rows (lf4);
+//   apply    -- cheap: the D-scan step or the children pushes that use them.
+// A lane that finishes a read takes the next one at once, so the lanes of a
+// warp keep doing the same expensive step together, whatever reads they hold.
+// Once the read queue is empty, a lane without work takes the bottom entry of
+// a busy lane's stack (its shallowest, usually largest, pending subtree) with
+// that read's context, searches it as a helper and hands its candidates back to
+// the owner, which finishes a pass only when every handed-out subtree has come
+// back (warp-level redistribution of backtracking work by ballot and shuffle).
+// The search (strands, D, children, limits, iterative deepening, reduction) is
+// that of aln_search.cuh; results are identical.
+#pragma once
+
+#include "aln_search.cuh"
+
+namespace aln {
+
+enum : uint32_t { PH_IDLE = 0, PH_DSCAN = 1, PH_DFS = 2, PH_DONE = 3, PH_FREE = 4, PH_WAIT = 5, PH_RETURN = 6 };
+enum : uint32_t { ROLE_OWN = 0, ROLE_HELP = 1 };
+enum : uint32_t { F_NONE = 0, F_OCC = 1, F_TABLE = 2 };
+
+// First entry of level j (strings of length j) in the prefix-trie table.
+__device__ __forceinline__ uint32_t trie_off(uint32_t j) { return ((1u << (2 * j)) - 4u) / 3u; }
+
+struct FetchReq {
+    uint32_t kind;    // F_NONE, F_OCC, F_TABLE
+    uint32_t text;    // 0 = X, 1 = X reversed
+    uint32_t lo, hi;  // F_OCC: the interval
+    uint32_t toff;    // F_TABLE: first of the four children entries
+};
+
+template <int STACK_CAP>
+struct FlatLane {
+    uint4 *stk;               // STACK_CAP entries (lo, hi, info, target-string id), local memory
+    uint4 *cand;              // kCandCap candidates (lo, hi, key, -), local memory
+    uint4 next;               // the node the next pop would return, kept in registers
+    bool has_next;
+    uint32_t nc, flags, work;
+    uint32_t phase, r, m, z, s, K;
+    int dj;
+    uint32_t dcnt, dlo, dhi, dsl, dsid;  // D scan: interval, segment length and id
+    uint32_t bpa0, bpa1, bpb0, bpb1;     // D breakpoints of strand 0 (a) and strand 1 (b)
+    uint32_t d00, d01;                   // D(0) of strand 0 and strand 1
+    uint32_t B;
+    int sp;
+    uint4 cur;                           // node being expanded across the fetch
+    uint32_t cbits;                      // its decisions
+    uint32_t role, owner;                // own read, or helper for the read of lane `owner`
+    uint32_t outstanding;                // owner: subtrees handed out and not yet returned
+    int base;                            // stack bottom (entries below were handed out)
+    uint32_t ret_i;                      // helper: next candidate to hand back
+    ReadView rv;                         // bases of the read being searched
+    ReadView own_rv;                     // this lane's shared-memory read columns
+#ifdef ALN_STATS
+    unsigned long long st_reads = 0, st_rounds = 0, st_pops = 0;
+#endif
+
+    __device__ __forceinline__ void add_cand(uint32_t lo, uint32_t hi, uint32_t key) {
+        for (uint32_t j = 0; j < nc; j++) {
+            const uint4 c = cand[j];
+            if (c.x == lo && c.y == hi && (c.z >> 31) == (key >> 31)) {
+                if (key < c.z) cand[j].z = key;
+                return;
+            }
+        }
+        if (nc < kCandCap) cand[nc++] = make_uint4(lo, hi, key, 0);
+        else flags |= ALN_FLAG_CAND_OVERFLOW;
+    }
+
+    __device__ __forceinline__ void record_fail() {
+        const uint32_t v = static_cast<uint32_t>(dj) + 1u;
+        const uint32_t sh = 8 * (dcnt & 3u);
+        if (s == 0) {
+            if (dcnt < 4) bpa0 |= v << sh;
+            else bpa1 |= v << sh;
+        } else {
+            if (dcnt < 4) bpb0 |= v << sh;
+            else bpb1 |= v << sh;
+        }
+        dcnt++;
+    }
+
+    __device__ __forceinline__ void write_result(aln_read_result *res, aln_hit *hits, const SearchParams &p,
+                                                 bool any, uint32_t final_b) {
+        aln_read_result out;
+        out.c0 = out.c1 = 0;
+        out.n_hits = 0;
+        out.d_best = 255;
+        out.reserved = 0;
+        aln_hit *H = hits + static_cast<uint64_t>(r) * p.hit_cap;
+        if (any) {
+            uint32_t kept = 0, dbest = 255;
+            for (uint32_t j = 0; j < nc; j++) {
+                const uint4 c = cand[j];
+                const uint32_t d = (c.z >> 28) & 7u;
+                if (d <= final_b) {
+                    cand[kept++] = c;
+                    dbest = min(dbest, d);
+                }
+            }
+            unsigned long long c0 = 0, c1 = 0;
+            for (uint32_t j = 0; j < kept; j++) {
+                const uint4 c = cand[j];
+                const uint32_t d = (c.z >> 28) & 7u;
+                if (d == dbest) c0 += c.y - c.x;
+                else if (d == dbest + 1) c1 += c.y - c.x;
+            }
+            out.c0 = c0 > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(c0);
+            out.c1 = c1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(c1);
+            out.d_best = static_cast<uint8_t>(kept ? dbest : 255);
+            const uint32_t nout = min(kept, p.hit_cap);
+            if (kept > p.hit_cap) flags |= ALN_FLAG_HIT_OVERFLOW;
+            for (uint32_t t = 0; t < nout; t++) {  // order (diffs, strand, k, l): selection
+                uint32_t best = t;
+                uint4 cb = cand[t];
+                for (uint32_t j = t + 1; j < kept; j++) {
+                    const uint4 cj = cand[j];
+                    const uint32_t kb = ((cb.z >> 28) & 7u) << 1 | (cb.z >> 31);
+                    const uint32_t kj = ((cj.z >> 28) & 7u) << 1 | (cj.z >> 31);
+                    if (kj < kb || (kj == kb && (cj.x < cb.x || (cj.x == cb.x && cj.y < cb.y)))) {
+                        best = j;
+                        cb = cj;
+                    }
+                }
+                cand[best] = cand[t];
+                cand[t] = cb;
+                aln_hit h;
+                const uint32_t key = cb.z;
+                h.k = cb.x;
+                h.l = cb.y - 1;
+                h.aligned_len = static_cast<uint16_t>(key & 0xFFFFu);
+                h.strand = static_cast<uint8_t>(key >> 31);
+                h.n_diff = static_cast<uint8_t>((key >> 28) & 7u);
+                h.n_gapo = static_cast<uint8_t>((key >> 24) & 15u);
+                h.n_gape = static_cast<uint8_t>((key >> 20) & 15u);
+                h.n_mm = static_cast<uint8_t>((key >> 16) & 15u);
+                h.reserved = 0;
+                H[t] = h;
+            }
+            out.n_hits = static_cast<uint8_t>(nout);
+        }
+        out.flags = static_cast<uint8_t>(flags);
+        res[r] = out;
+        phase = PH_IDLE;
+#ifdef ALN_STATS
+        st_reads++;
+#endif
+    }
+
+    __device__ __forceinline__ void start_strand(uint32_t n, uint32_t strand) {
+        s = strand;
+        sp = 0;
+        base = 0;
+        has_next = false;
+        if ((strand ? d01 : d00) <= B) {
+            next = make_uint4(0, n + 1, pack_info(0, 0, 0, 0, 0, 0, OP_M), 0);
+            has_next = true;
+        }
+    }
+
+    __device__ __forceinline__ void start_pass(uint32_t n, uint32_t budget) {
+        B = budget;
+        nc = 0;
+        phase = PH_DFS;
+        start_strand(n, 0);
+    }
+
+    __device__ __forceinline__ void push_mem(const uint4 &e) {
+        if (sp == STACK_CAP && base > 0) {  // slide the live entries down over handed-out ones
+            for (int j = base; j < sp; j++) stk[j - base] = stk[j];
+            sp -= base;
+            base = 0;
+        }
+        if (sp < STACK_CAP) stk[sp++] = e;
+        else flags |= ALN_FLAG_STACK_OVERFLOW;
+    }
+
+    // Push a child; the newest child is held in `next` (it is what the next pop
+    // would return), the one it displaces goes to the stack.
+    __device__ __forceinline__ void push(uint32_t lo, uint32_t hi, uint32_t info, uint32_t id) {
+        if (has_next) push_mem(next);
+        next = make_uint4(lo, hi, info, id);
+        has_next = true;
+    }
+
+    // Children of the node in cur / cbits given its four extensions.
+    __device__ __forceinline__ void push_children(const uint32_t lo4[4], const uint32_t hi4[4]) {
+        const uint32_t info = cur.z;
+        const uint32_t i = info & 0xFFu, mm = (info >> 8) & 7u, go = (info >> 11) & 7u, ge = (info >> 14) & 7u;
+        const uint32_t ni = (info >> 17) & 7u, sd = (info >> 20) & 7u, last = (info >> 23) & 3u;
+        const bool allowM = cbits & 1u, mm_ok = cbits & 2u, ins_ok = cbits & 4u, del_ok = cbits & 8u;
+        const uint32_t qi = (cbits >> 4) & 3u;
+        const bool isN = cbits & 64u;
+        const uint32_t sd2 = sd + ((cbits >> 7) & 1u);
+        const bool grow = cbits & 256u;  // the node's target is shorter than k: track child ids
+        const uint32_t cid = grow ? cur.w << 2 : 0u;
+        const uint32_t mlo = qi == 0 ? lo4[0] : (qi == 1 ? lo4[1] : (qi == 2 ? lo4[2] : lo4[3]));
+        const uint32_t mhi = qi == 0 ? hi4[0] : (qi == 1 ? hi4[1] : (qi == 2 ? hi4[2] : hi4[3]));
+        if (allowM && mhi > mlo) push(mlo, mhi, pack_info(i + 1, mm, go, ge, ni, sd, OP_M), cid | qi);
+        if (mm_ok) {
+#pragma unroll
+            for (uint32_t c = 0; c < 4; c++)
+                if ((c != qi || isN) && hi4[c] > lo4[c])
+                    push(lo4[c], hi4[c], pack_info(i + 1, mm + 1, go, ge, ni, sd2, OP_M), cid | c);
+        }
+        if (ins_ok)
+            push(cur.x, cur.y,
+                 last == OP_I ? pack_info(i + 1, mm, go, ge + 1, ni + 1, sd2, OP_I)
+                              : pack_info(i + 1, mm, go + 1, ge, ni + 1, sd2, OP_I),
+                 cur.w);
+        if (del_ok) {
+#pragma unroll
+            for (uint32_t c = 0; c < 4; c++)
+                if (hi4[c] > lo4[c])
+                    push(lo4[c], hi4[c],
+                         last == OP_D ? pack_info(i, mm, go, ge + 1, ni, sd2, OP_D)
+                                      : pack_info(i, mm, go + 1, ge, ni, sd2, OP_D),
+                         cid | c);
+        }
+    }
+
+    // Control: advance until the lane needs the four extensions of an interval
+    // (fills fr) or is done.  Each round does O(1) work; the rounds are bounded.
+    __device__ __forceinline__ void control(const DIndex &X, const ReadBatch &rb, uint32_t n_reads,
+                                            const SearchParams &p, aln_read_result *res, aln_hit *hits,
+                                            uint32_t *queue, uint32_t *sb, uint32_t *sn, FetchReq &fr) {
+        const uint32_t n = X.t[0].n;  // both texts have the same length
+        fr.kind = F_NONE;
+        for (int round = 0; round < 32; round++) {
+            if (phase == PH_DONE || phase == PH_FREE || phase == PH_RETURN) return;
+            if (phase == PH_WAIT) {
+                if (outstanding) return;
+                phase = PH_DFS;
+            }
+#ifdef ALN_STATS
+            st_rounds++;
+#endif
+            if (phase == PH_IDLE) {
+                r = atomicAdd(queue, 1u);
+                if (r >= n_reads) {
+                    phase = PH_FREE;
+                    return;
+                }
+                role = ROLE_OWN;
+                rv = own_rv;
+                m = rb.len[r];
+                z = rb.z ? rb.z[r] : p.z;
+                flags = 0;
+                work = 0;
+                nc = 0;
+                if (m > ALN_MAX_READ_LEN) flags |= ALN_FLAG_READ_TOO_LONG;
+                if (z > ALN_MAX_Z || z > p.z) flags |= ALN_FLAG_BAD_LIMIT;
+                if (flags || m == 0) {
+                    write_result(res, hits, p, false, 0);
+                    continue;
+                }
+                load_read(rb, rb.offset[r], m, sb, sn);
+                phase = PH_DSCAN;
+                s = 0;
+                dj = static_cast<int>(m) - 1;
+                dcnt = 0;
+                dlo = 0;
+                dhi = n + 1;
+                dsl = 0;
+                dsid = 0;
+                bpa0 = bpa1 = bpb0 = bpb1 = 0;
+                continue;
+            }
+            if (phase == PH_DSCAN) {
+                const uint32_t zcap = min(z + 1, 8u);
+                if (dj < 0 || dcnt >= zcap) {
+                    if (s == 0) {
+                        d00 = d_at(bpa0, bpa1, 0);
+                        s = 1;
+                        dj = static_cast<int>(m) - 1;
+                        dcnt = 0;
+                        dlo = 0;
+                        dhi = n + 1;
+                        dsl = 0;
+                        dsid = 0;
+                        continue;
+                    }
+                    d01 = d_at(bpb0, bpb1, 0);
+                    const uint32_t lb = min(d00, d01);
+                    if (lb > z) {
+                        write_result(res, hits, p, false, 0);
+                        continue;
+                    }
+                    start_pass(n, p.strata == ALN_STRATA_FULL ? z : min(z, lb + 1));
+                    continue;
+                }
+                // strand 0's D comes from X, strand 1's from X reversed
+                const uint32_t c = rv.base(static_cast<uint32_t>(dj)) ^ (s ? 3u : 0u);
+                bool fail = rv.isN(static_cast<uint32_t>(dj));
+                if (!fail && dsl == 0) {  // from the empty string: the C ranges
+                    dlo = s ? X.t[1].C1[c] : X.t[0].C1[c];
+                    dhi = s ? X.t[1].C1[c + 1] : X.t[0].C1[c + 1];
+                    fail = dhi <= dlo;
+                    if (!fail) {
+                        dsl = 1;
+                        dsid = c;
+                        dj--;
+                        continue;
+                    }
+                }
+                if (fail) {
+                    record_fail();
+                    dlo = 0;
+                    dhi = n + 1;
+                    dsl = 0;
+                    dsid = 0;
+                    dj--;
+                    continue;
+                }
+                fr.text = s;
+                if (dsl < K) {
+                    fr.kind = F_TABLE;
+                    fr.toff = trie_off(dsl + 1) + (dsid << 2);
+                } else {
+                    fr.kind = F_OCC;
+                    fr.lo = dlo;
+                    fr.hi = dhi;
+                }
+                return;
+            }
+            // PH_DFS
+            if (!has_next && sp == base) {
+                sp = base = 0;
+                if (role == ROLE_HELP) {  // subtree done: hand the candidates back
+                    phase = PH_RETURN;
+                    ret_i = 0;
+                    return;
+                }
+                if (outstanding) {  // wait for handed-out subtrees before the pass ends
+                    phase = PH_WAIT;
+                    return;
+                }
+                if (s == 0) {
+                    start_strand(n, 1);
+                    continue;
+                }
+                if ((flags & ALN_FLAG_WORK_LIMIT) || p.strata == ALN_STRATA_FULL) {
+                    write_result(res, hits, p, nc > 0, z);
+                    continue;
+                }
+                if (nc == 0) {
+                    if (B >= z) {
+                        write_result(res, hits, p, false, 0);
+                        continue;
+                    }
+                    start_pass(n, min(z, B + 2));
+                    continue;
+                }
+                uint32_t dmin = 255;
+                for (uint32_t j = 0; j < nc; j++) dmin = min(dmin, (cand[j].z >> 28) & 7u);
+                const uint32_t F = min(z, dmin + 1);
+                if (F <= B) {
+                    write_result(res, hits, p, true, F);
+                    continue;
+                }
+                start_pass(n, F);
+                continue;
+            }
+            if (++work > p.work_limit) {
+                flags |= ALN_FLAG_WORK_LIMIT;
+                sp = base;
+                has_next = false;
+                if (role == ROLE_OWN) s = 1;
+                continue;
+            }
+            uint4 e;
+            if (has_next) {
+                e = next;
+                has_next = false;
+            } else {
+                e = stk[--sp];
+            }
+#ifdef ALN_STATS
+            st_pops++;
+#endif
+            const uint32_t info = e.z;
+            const uint32_t i = info & 0xFFu, mm = (info >> 8) & 7u, go = (info >> 11) & 7u, ge = (info >> 14) & 7u;
+            const uint32_t ni = (info >> 17) & 7u, sd = (info >> 20) & 7u, last = (info >> 23) & 3u;
+            const uint32_t diffs = mm + go + ge;
+            const uint32_t rem = B - diffs;
+            if (i == m) {
+                const uint32_t alen = m + (go + ge - ni) - ni;
+                if (alen >= 1)
+                    add_cand(e.x, e.y, (s << 31) | (diffs << 28) | (go << 24) | (ge << 20) | (mm << 16) | alen);
+                continue;
+            }
+            const uint32_t bp0 = s ? bpb0 : bpa0, bp1 = s ? bpb1 : bpa1;
+            const bool isN = rv.isN(i);
+            const uint32_t qi = rv.base(i) ^ (s ? 3u : 0u);
+            const uint32_t Dn = d_at(bp0, bp1, i + 1), Di = d_at(bp0, bp1, i);
+            const uint32_t e1 = p.e < 1 ? 1 : p.e;
+            const bool in_seed = p.seed_len && i < p.seed_len;
+            const bool alt = rem >= 1 && (!in_seed || sd < p.seed_z);
+            const bool allowM = !isN && rem >= Dn;
+            const bool mm_ok = alt && rem - 1 >= Dn;
+            const bool ins_ok = alt && rem - 1 >= Dn && i >= p.e && i + 1 + p.e <= m && last != OP_D &&
+                                (last == OP_I ? ge < p.max_gape : go < p.max_gapo);
+            const bool del_ok = alt && rem - 1 >= Di && i >= e1 && i + e1 <= m && last != OP_I &&
+                                (last == OP_D ? ge < p.max_gape : go < p.max_gapo);
+            const uint32_t L = i + go + ge - 2 * ni;  // target length: consumed + deleted - inserted
+            cur = e;
+            cbits = (allowM ? 1u : 0u) | (mm_ok ? 2u : 0u) | (ins_ok ? 4u : 0u) | (del_ok ? 8u : 0u) | (qi << 4) |
+                    (isN ? 64u : 0u) | (in_seed ? 128u : 0u) | (L < K ? 256u : 0u);
+            if (!(allowM || mm_ok || del_ok)) {
+                if (ins_ok) {
+                    const uint32_t z4[4] = {0, 0, 0, 0};
+                    push_children(z4, z4);  // only the insertion child
+                }
+                continue;
+            }
+            if (L == 0) {  // empty target: children are the C ranges
+                uint32_t lo4[4], hi4[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    lo4[c] = s ? X.t[0].C1[c] : X.t[1].C1[c];
+                    hi4[c] = s ? X.t[0].C1[c + 1] : X.t[1].C1[c + 1];
+                }
+                push_children(lo4, hi4);
+                continue;
+            }
+            fr.text = s ? 0u : 1u;  // strand 0 searches X reversed, strand 1 searches X
+            if (L < K) {
+                fr.kind = F_TABLE;
+                fr.toff = trie_off(L + 1) + (e.w << 2);
+            } else {
+                fr.kind = F_OCC;
+                fr.lo = e.x;
+                fr.hi = e.y;
+            }
+            return;
+        }
+    }
+
+    // Warp-synchronous hand-over, once per trip, all 32 lanes: returning helpers
+    // send one candidate (or their completion) to the owner; free lanes take the
+    // bottom stack entry of a lane with at least two pending entries.
+    __device__ __forceinline__ void exchange(uint32_t lane, const uint32_t *sbase, const uint32_t *snbase,
+                                             uint32_t warp_col) {
+        const unsigned FULL = 0xFFFFFFFFu;
+        unsigned ret = __ballot_sync(FULL, phase == PH_RETURN);
+        while (ret) {
+            const uint32_t src = __ffs(ret) - 1;
+            ret &= ret - 1;
+            const bool mine = lane == src;
+            const uint32_t o = __shfl_sync(FULL, owner, src);
+            const uint32_t has = __shfl_sync(FULL, (mine && ret_i < nc) ? 1u : 0u, src);
+            const uint4 c = (mine && ret_i < nc) ? cand[ret_i] : make_uint4(0, 0, 0, 0);
+            const uint32_t cx = __shfl_sync(FULL, c.x, src), cy = __shfl_sync(FULL, c.y, src),
+                           cz = __shfl_sync(FULL, c.z, src);
+            const uint32_t hf = __shfl_sync(FULL, flags, src);
+            if (lane == o) {
+                if (has) add_cand(cx, cy, cz);
+                else {
+                    outstanding--;
+                    flags |= hf & ALN_FLAG_INCOMPLETE;
+                }
+            }
+            if (mine) {
+                if (has) ret_i++;
+                else {
+                    phase = PH_FREE;
+                    role = ROLE_OWN;
+                    rv = own_rv;
+                }
+            }
+        }
+        unsigned freem = __ballot_sync(FULL, phase == PH_FREE);
+        unsigned donm = __ballot_sync(FULL, phase == PH_DFS && (sp - base >= 2 || (sp - base >= 1 && has_next)));
+        while (freem && donm) {
+            const uint32_t rcv = __ffs(freem) - 1, dnr = __ffs(donm) - 1;
+            freem &= freem - 1;
+            donm &= donm - 1;
+            const bool give = lane == dnr;
+            const uint4 e = give ? stk[base] : make_uint4(0, 0, 0, 0);
+            const uint32_t ex = __shfl_sync(FULL, e.x, dnr), ey = __shfl_sync(FULL, e.y, dnr);
+            const uint32_t ez = __shfl_sync(FULL, e.z, dnr), ew = __shfl_sync(FULL, e.w, dnr);
+            const uint32_t o = __shfl_sync(FULL, role == ROLE_OWN ? lane : owner, dnr);
+            const uint32_t hm = __shfl_sync(FULL, m, dnr), hB = __shfl_sync(FULL, B, dnr);
+            const uint32_t hs = __shfl_sync(FULL, s, dnr), hz = __shfl_sync(FULL, z, dnr);
+            const uint32_t h0 = __shfl_sync(FULL, s ? bpb0 : bpa0, dnr);
+            const uint32_t h1 = __shfl_sync(FULL, s ? bpb1 : bpa1, dnr);
+            if (give) base++;
+            if (lane == o) outstanding++;
+            if (lane == rcv) {
+                role = ROLE_HELP;
+                owner = o;
+                m = hm;
+                B = hB;
+                s = hs;
+                z = hz;
+                if (hs) { bpb0 = h0; bpb1 = h1; } else { bpa0 = h0; bpa1 = h1; }
+                next = make_uint4(ex, ey, ez, ew);
+                has_next = true;
+                sp = 0;
+                base = 0;
+                nc = 0;
+                work = 0;
+                flags = 0;
+                phase = PH_DFS;
+                rv = ReadView{sbase + warp_col + o, snbase + warp_col + o};
+            }
+        }
+    }
+
+    __device__ __forceinline__ void apply(const DIndex &X, const uint32_t lo4[4], const uint32_t hi4[4]) {
+        if (phase == PH_DSCAN) {
+            const uint32_t c = rv.base(static_cast<uint32_t>(dj)) ^ (s ? 3u : 0u);
+            dlo = c == 0 ? lo4[0] : (c == 1 ? lo4[1] : (c == 2 ? lo4[2] : lo4[3]));
+            dhi = c == 0 ? hi4[0] : (c == 1 ? hi4[1] : (c == 2 ? hi4[2] : hi4[3]));
+            if (dhi <= dlo) {
+                record_fail();
+                dlo = 0;
+                dhi = X.t[0].n + 1;
+                dsl = 0;
+                dsid = 0;
+            } else {
+                dsid = dsl < K ? (dsid << 2) | c : 0u;
+                dsl++;
+            }
+            dj--;
+        } else {
+            push_children(lo4, hi4);
+        }
+    }
+};
+
+// The four extensions for a fetch request (table group or Occ blocks).
+__device__ __forceinline__ void fetch4(const DIndex &X, const FetchReq &fr, uint32_t lo4[4], uint32_t hi4[4]) {
+    const DText T = fr.text ? X.t[1] : X.t[0];
+    if (fr.kind == F_TABLE) {
+        const uint4 *g = reinterpret_cast<const uint4 *>(T.kmer + fr.toff);
+        const uint4 a = ld_nc(g), b = ld_nc(g + 1);
+        lo4[0] = a.x; hi4[0] = a.y; lo4[1] = a.z; hi4[1] = a.w;
+        lo4[2] = b.x; hi4[2] = b.y; lo4[3] = b.z; hi4[3] = b.w;
+    } else {
+        lf4(T, fr.lo, fr.hi, lo4, hi4);
+    }
+}
+
+}  // namespace aln

@@ -16,9 +16,20 @@
 
 #include <string>
 
+#include "aln_flat.cuh"
 #include "aln_search.cuh"
 
 namespace aln {
+
+#ifdef ALN_STATS
+// Instrumented build only: event counters of the persistent kernel.
+//  0 loop iterations (lane)   1 fetch iterations (lane)   2 Occ fetches
+//  3 table fetches            4 warp-level fetch issues    5 lanes at those issues
+//  6 reads finished           7 control rounds             8 stack pops
+//  9 warp trips                10 live lanes at those trips
+__device__ unsigned long long g_stats[16];
+#define STAT_ADD(i, v) atomicAdd(&g_stats[i], static_cast<unsigned long long>(v))
+#endif
 
 template <int STACK_CAP>
 __global__ void __launch_bounds__(kThreads) aln_plain_kernel(DIndex X, ReadBatch rb, uint32_t n_reads, SearchParams p,
@@ -35,24 +46,89 @@ __global__ void __launch_bounds__(kThreads) aln_plain_kernel(DIndex X, ReadBatch
     S.run(X, rv, m, z, p, res + r, hits + static_cast<uint64_t>(r) * p.hit_cap);
 }
 
+#ifndef ALN_PERSISTENT_MIN_BLOCKS
+#define ALN_PERSISTENT_MIN_BLOCKS 6  // 80 registers: 6 resident blocks per SM measured best
+#endif
+
 template <int STACK_CAP>
-__global__ void __launch_bounds__(kThreads) aln_persistent_kernel(DIndex X, ReadBatch rb, uint32_t n_reads,
+__global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persistent_kernel(DIndex X, ReadBatch rb, uint32_t n_reads,
                                                                   SearchParams p, aln_read_result *res,
                                                                   aln_hit *hits, uint32_t *queue) {
     __shared__ uint32_t s_bases[kReadWords * kThreads];
     __shared__ uint32_t s_nmask[kMaskWords * kThreads];
-    ReadView rv{s_bases + threadIdx.x, s_nmask + threadIdx.x};
-    Search<STACK_CAP> S;
-    // bounded: each iteration consumes one queue ticket, at most n_reads + grid
-    for (uint32_t guard = 0; guard <= n_reads; guard++) {
-        const uint32_t r = atomicAdd(queue, 1u);
-        if (r >= n_reads) break;
-        const uint32_t m = rb.len[r];
-        const uint32_t z = rb.z ? rb.z[r] : p.z;
-        if (m <= ALN_MAX_READ_LEN && m > 0) load_read(rb, rb.offset[r], m, s_bases + threadIdx.x, s_nmask + threadIdx.x);
-        S.run(X, rv, m, z, p, res + r, hits + static_cast<uint64_t>(r) * p.hit_cap);
+    uint32_t *sb = s_bases + threadIdx.x, *sn = s_nmask + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u, warp_col = threadIdx.x & ~31u;
+    uint4 stk[STACK_CAP], cand[kCandCap];
+    FlatLane<STACK_CAP> L;
+    L.stk = stk;
+    L.cand = cand;
+    L.has_next = false;
+    L.phase = PH_IDLE;
+    L.r = 0xFFFFFFFFu;
+    L.sp = 0;
+    L.base = 0;
+    L.K = X.kmer_k;
+    L.role = ROLE_OWN;
+    L.owner = lane;
+    L.outstanding = 0;
+    L.own_rv = ReadView{sb, sn};
+    L.rv = L.own_rv;
+#ifdef ALN_STATS
+    unsigned long long st_it = 0, st_f = 0, st_occ = 0, st_tab = 0, st_wi = 0, st_wl = 0, st_wa = 0, st_wal = 0;
+#endif
+    // All 32 lanes of the warp stay in the loop until every lane is free and the
+    // queue is empty; each trip is: control, one converged fetch, the hand-over.
+    // Finite: every read costs at most 2 x 256 D steps and z + 2 passes of at
+    // most work_limit expansions; the guard only caps a bug.
+    for (unsigned long long it = 0; it < (1ull << 44); it++) {
+        FetchReq fr;
+        L.control(X, rb, n_reads, p, res, hits, queue, sb, sn, fr);
+        __syncwarp();
+#ifdef ALN_STATS
+        st_it++;
+        {
+            const unsigned busy = __ballot_sync(0xFFFFFFFFu, L.phase != PH_FREE);
+            if (lane == 0) {
+                st_wa++;
+                st_wal += __popc(busy);
+            }
+        }
+#endif
+        if (fr.kind != F_NONE) {
+#ifdef ALN_STATS
+            const unsigned am = __activemask();
+            st_f++;
+            st_occ += fr.kind == F_OCC;
+            st_tab += fr.kind == F_TABLE;
+            if (lane == __ffs(am) - 1) {
+                st_wi++;
+                st_wl += __popc(am);
+            }
+#endif
+            uint32_t lo4[4], hi4[4];
+            fetch4(X, fr, lo4, hi4);
+            L.apply(X, lo4, hi4);
+        }
+        L.exchange(lane, s_bases, s_nmask, warp_col);
+        if (__ballot_sync(0xFFFFFFFFu, L.phase != PH_FREE) == 0) break;
     }
+#ifdef ALN_STATS
+    STAT_ADD(0, st_it); STAT_ADD(1, st_f); STAT_ADD(2, st_occ); STAT_ADD(3, st_tab);
+    STAT_ADD(4, st_wi); STAT_ADD(5, st_wl); STAT_ADD(6, L.st_reads); STAT_ADD(7, L.st_rounds);
+    STAT_ADD(8, L.st_pops); STAT_ADD(9, st_wa); STAT_ADD(10, st_wal);
+#endif
 }
+
+#ifdef ALN_STATS
+cudaError_t debug_stats(unsigned long long *out, int reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_stats, sizeof(g_stats));
+    if (e == cudaSuccess && reset) {
+        unsigned long long z[16] = {};
+        e = cudaMemcpyToSymbol(g_stats, z, sizeof(z));
+    }
+    return e;
+}
+#endif
 
 int stack_cap_for(uint32_t z) { return z <= 2 ? 19 : (z <= 4 ? 37 : 64); }
 
@@ -68,6 +144,7 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<CAP>, kThreads, 0);
+        if (p.blocks_per_sm && static_cast<int>(p.blocks_per_sm) < per_sm) per_sm = p.blocks_per_sm;
         if (per_sm < 1) per_sm = 1;
         uint32_t blocks = static_cast<uint32_t>(sms * per_sm);
         const uint32_t need = (n + kThreads - 1) / kThreads;

@@ -46,7 +46,7 @@ struct ReadBatch {
 };
 
 struct SearchParams {
-    uint32_t z, max_gapo, max_gape, seed_len, seed_z, e, hit_cap, strata, work_limit;
+    uint32_t z, max_gapo, max_gape, seed_len, seed_z, e, hit_cap, strata, work_limit, blocks_per_sm;
 };
 
 // Stack-entry info word: i (8) | n_mm (3) | n_gapo (3) | n_gape (3) | n_ins (3) | seed (3) | last (2)

@@ -10,9 +10,10 @@
 // groups are singletons.  Groups are processed in parallel.
 //
 // Occ layout: 64-byte blocks of 192 rows, [cnt_A cnt_C cnt_G cnt_T | 12 words of
-// 2-bit symbols], counts taken before the block's first row with $ counted as A
-// (the $ row is stored as A; a query subtracts one from Occ(A) past the primary
-// row).  One LF step reads one block per row, usually one sector pair.
+// 2-bit symbols].  The counts are taken at the block's middle row (192 b + 96),
+// with $ counted as A, so a query counts at most 96 symbols (6 words) forwards
+// or backwards from there; the $ row is stored as A and a query subtracts one
+// from Occ(A) past the primary row.  One LF step reads one 64-byte block per row.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -242,47 +243,61 @@ static void pack_text(HostText &T, const uint8_t *y, uint64_t n, const uint32_t 
             for (int c = 0; c < 4; c++) bcount[b * 4 + c] = c4[c];
         }
     });
+    // counts before the middle row: prefix over earlier blocks + the block's first
+    // half.  Padding past the last row is stored as A and counted here too, so a
+    // backward count from the middle of the last block stays exact.
     uint32_t run[4] = {0, 0, 0, 0};
-    for (uint64_t b = 0; b < nb; b++)
+    for (uint64_t b = 0; b < nb; b++) {
+        uint32_t half[4] = {0, 0, 0, 0};
+        for (uint32_t t = 0; t < kBlockRows / 2; t++)
+            half[(T.blocks[b * kBlockWords + 4 + t / 16] >> (2 * (t % 16))) & 3u]++;
         for (int c = 0; c < 4; c++) {
-            T.blocks[b * kBlockWords + c] = run[c];
+            T.blocks[b * kBlockWords + c] = run[c] + half[c];
             run[c] += bcount[b * 4 + c];
         }
+    }
     const uint64_t ns = n / sa_sample + 1;
     T.sa_samp.resize(ns);
     for (uint64_t t = 0; t < ns; t++) T.sa_samp[t] = sa[t * sa_sample];
 }
 
-// Table of half-open SA intervals of every k-mer, indexed by the k symbols in
-// the order a backward search processes them (first processed symbol in the top
-// bits): processing q[0], ..., q[k-1] reaches the rows whose suffix starts with
-// q[k-1] ... q[0].  Rows of one k-mer are contiguous in the SA, so one scan over
-// the SA finds every interval.  Absent k-mers get (0, 0).
+// Interval table of every string of length 1..k (a prefix trie of the index).
+// A search extends its target one base at a time, so a node's interval is a
+// function of its target string alone; indexing strings in the order the search
+// processes them (first processed base in the top bits) puts the four children
+// of a string s at 4 s + c, contiguous, one level down.  Level j (1..k) starts at
+// entry (4^j - 4) / 3 and holds 4^j half-open (lo, hi) pairs; absent strings get
+// (0, 0).  Rows sharing a j-prefix are contiguous in the SA, so one scan over
+// the SA fills every level: for the suffix at s, the string processed as
+// q[0..j-1] is y[s+j-1] .. y[s] and its index is sum_u y[s+u] 4^u.
 static void build_kmer(HostText &T, const uint8_t *y, uint64_t n, const uint32_t *sa, uint32_t k,
                        int threads) {
-    const uint64_t cnt = 1ULL << (2 * k);
-    T.kmer.assign(2 * cnt, 0);
+    const uint64_t total = ((1ULL << (2 * (k + 1))) - 4) / 3;
+    T.kmer.assign(2 * total, 0);
     const uint64_t rows = n + 1;
-    auto id_of = [&](uint64_t r) -> int64_t {
-        uint64_t s = sa[r];
-        if (s + k > n) return -1;
-        uint64_t id = 0;
-        for (uint32_t t = 0; t < k; t++) id |= uint64_t(y[s + t]) << (2 * t);  // y[s+t] is q[k-1-t]
-        return static_cast<int64_t>(id);
-    };
-    parallel_chunks(threads, rows, [&](int, uint64_t b, uint64_t e) {
-        int64_t prev = b > 0 ? id_of(b - 1) : -2;
-        int64_t cur = id_of(b);
-        for (uint64_t r = b; r < e; r++) {
-            int64_t nxt = r + 1 < rows ? id_of(r + 1) : -2;
-            if (cur >= 0) {
-                if (cur != prev) T.kmer[2 * cur] = static_cast<uint32_t>(r);
-                if (cur != nxt) T.kmer[2 * cur + 1] = static_cast<uint32_t>(r + 1);
+    for (uint32_t j = 1; j <= k; j++) {
+        const uint64_t off = ((1ULL << (2 * j)) - 4) / 3;
+        auto id_of = [&](uint64_t r) -> int64_t {
+            uint64_t s = sa[r];
+            if (s + j > n) return -1;
+            uint64_t id = 0;
+            for (uint32_t u = 0; u < j; u++) id |= uint64_t(y[s + u]) << (2 * u);
+            return static_cast<int64_t>(id);
+        };
+        parallel_chunks(threads, rows, [&](int, uint64_t b, uint64_t e) {
+            int64_t prev = b > 0 ? id_of(b - 1) : -2;
+            int64_t cur = id_of(b);
+            for (uint64_t r = b; r < e; r++) {
+                int64_t nxt = r + 1 < rows ? id_of(r + 1) : -2;
+                if (cur >= 0) {
+                    if (cur != prev) T.kmer[2 * (off + cur)] = static_cast<uint32_t>(r);
+                    if (cur != nxt) T.kmer[2 * (off + cur) + 1] = static_cast<uint32_t>(r + 1);
+                }
+                prev = cur;
+                cur = nxt;
             }
-            prev = cur;
-            cur = nxt;
-        }
-    });
+        });
+    }
 }
 
 }  // namespace aln
@@ -344,7 +359,9 @@ extern "C" int fm_index_info(const fm_index *idx, fm_index_info_t *info) {
     return ALN_OK;
 }
 
-static const char kMagic[8] = {'A', 'L', 'N', 'F', 'M', 'I', 'X', '1'};
+static uint64_t kmer_words(uint32_t k) { return k ? 2 * (((1ULL << (2 * (k + 1))) - 4) / 3) : 0; }
+
+static const char kMagic[8] = {'A', 'L', 'N', 'F', 'M', 'I', 'X', '3'};
 
 template <class V>
 static bool write_vec(std::ofstream &f, const V &v) {
@@ -411,8 +428,8 @@ extern "C" int fm_index_load(const char *path, fm_index **out) {
             const uint64_t nb = (T.n + 1) / kBlockRows + 1;
             ok = read_vec(f, T.blocks, nb * kBlockWords) && T.blocks.size() == nb * kBlockWords &&
                  read_vec(f, T.sa_samp, T.n + 1) && T.sa_samp.size() == T.n / ix->sa_sample + 1 &&
-                 read_vec(f, T.kmer, ix->kmer_k ? (2ULL << (2 * ix->kmer_k)) : 0) &&
-                 T.kmer.size() == (ix->kmer_k ? (2ULL << (2 * ix->kmer_k)) : 0) && T.primary <= T.n;
+                 read_vec(f, T.kmer, kmer_words(ix->kmer_k)) && T.kmer.size() == kmer_words(ix->kmer_k) &&
+                 T.primary <= T.n;
         }
         if (!ok || ix->t[0].n != ix->t[1].n) {
             delete ix;

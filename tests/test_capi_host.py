@@ -45,7 +45,7 @@ def _read_index_file(path):
     text (n, primary, C[4]) and three length-prefixed u32 vectors."""
     with open(path, "rb") as f:
         data = f.read()
-    assert data[:8] == b"ALNFMIX1"
+    assert data[:8] == b"ALNFMIX3"
     off = 8
     sa_sample, kmer_k, n_seed = struct.unpack_from("<3Q", data, off)
     off += 24
@@ -100,22 +100,29 @@ def test_host_index_matches_oracle(tmp_path, name, n, kmer_k, sample):
         exp = bwt.copy()
         exp[exp == 4] = 0  # $ stored as A
         assert np.array_equal(dec, exp)
-        # block counts: occurrences before the block's first row, $ counted as A
-        rows = np.arange(T["blocks"].shape[0]) * 192
-        cs = np.zeros((t.size + 2, 4), np.int64)
+        # block counts: occurrences before the block's middle row, $ and the
+        # padding after the last row counted as A
+        nb = T["blocks"].shape[0]
+        padded = np.zeros(nb * 192, np.uint8)
+        padded[: exp.size] = exp
+        rows = np.arange(nb) * 192 + 96
+        cs = np.zeros((padded.size + 1, 4), np.int64)
         for c in range(4):
-            cs[1:, c] = np.cumsum(exp == c)
-        assert np.array_equal(T["blocks"][:, :4], cs[np.minimum(rows, t.size + 1)])
+            cs[1:, c] = np.cumsum(padded == c)
+        assert np.array_equal(T["blocks"][:, :4], cs[rows])
         assert np.array_equal(T["sa"], sa[::sample])
         if kmer_k:
             km = T["kmer"].reshape(-1, 2)
+            assert km.shape[0] == (4 ** (kmer_k + 1) - 4) // 3
             rng = np.random.default_rng(n + w)
-            for kid in list(rng.integers(0, 4 ** kmer_k, 200)) + [0, 4 ** kmer_k - 1]:
-                # processing order: first symbol in the top bits; pattern = reversed
-                q = [(int(kid) >> (2 * (kmer_k - 1 - j))) & 3 for j in range(kmer_k)]
-                iv = ox.exact(w, np.array(q[::-1], np.uint8))
-                exp_iv = (0, 0) if iv is None else (iv[0], iv[1] + 1)
-                assert tuple(km[kid]) == exp_iv
+            for j in range(1, kmer_k + 1):
+                off = (4 ** j - 4) // 3
+                for kid in list(rng.integers(0, 4 ** j, 60)) + [0, 4 ** j - 1]:
+                    # processing order: first symbol in the top bits; pattern = reversed
+                    q = [(int(kid) >> (2 * (j - 1 - u))) & 3 for u in range(j)]
+                    iv = ox.exact(w, np.array(q[::-1], np.uint8))
+                    exp_iv = (0, 0) if iv is None else (iv[0], iv[1] + 1)
+                    assert tuple(km[off + kid]) == exp_iv
     # load round trip
     idx2 = aln.Index.load(path)
     assert idx2.info() == info
@@ -147,7 +154,7 @@ def test_build_argument_errors():
     with pytest.raises(aln.AlnError):
         aln.Index.build(np.zeros(10, np.uint8), sa_sample=3)
     with pytest.raises(aln.AlnError):
-        aln.Index.build(np.zeros(10, np.uint8), kmer_k=14)
+        aln.Index.build(np.zeros(10, np.uint8), kmer_k=13)
     L = aln.lib()
     b = aln._lib.aln_batch()
     p = aln.Params().c()

@@ -11,6 +11,7 @@ from synth import Rng, Reads, reference_iid, simulate_reads, workload, z_for_len
 pytestmark = pytest.mark.gpu
 
 MODES = [aln.MODE_PLAIN, aln.MODE_PERSISTENT]
+BENCH_KMER = 11  # prefix-trie depth the benchmark uses
 
 
 @pytest.fixture(scope="module")
@@ -22,35 +23,42 @@ def cuda():
 
 
 class Pair:
-    """Product index on the device and the oracle's own index of the same text."""
+    """Product index on the device and the oracle's own index of the same text.
+    ``kmers`` lists prefix-trie depths; ``al`` uses the first, ``als[k]`` any."""
 
-    def __init__(self, text, kmer_k=0, n_seed=0):
+    def __init__(self, text, kmer_k=0, n_seed=0, kmers=None):
         self.text = text
         self.ox = oracle.OracleIndex(text, n_seed=n_seed)
-        self.hix = aln.Index.build(text, n_seed=n_seed, kmer_k=kmer_k)
-        self.dix = self.hix.to_device(0)
-        self.al = aln.Aligner(self.dix)
+        self.als = {}
+        for k in (kmers or [kmer_k]):
+            hix = aln.Index.build(text, n_seed=n_seed, kmer_k=k)
+            self.als[k] = aln.Aligner(hix.to_device(0))
+        self.al = self.als[(kmers or [kmer_k])[0]]
 
 
 @pytest.fixture(scope="module")
 def tiny36(cuda):
     w = workload("tiny36")
-    return w, Pair(w.text)
+    return w, Pair(w.text, kmers=[0, 10])
 
 
-def _run(pair, reads, lim, hit_cap=32, strata=aln.STRATA_BEST1, mode=aln.MODE_PLAIN, z=None, zmax=None):
+def _run(pair, reads, lim, hit_cap=32, strata=aln.STRATA_BEST1, mode=aln.MODE_PLAIN, z=None, zmax=None,
+         kmer=None):
     p = aln.Params.from_limits(lim, hit_cap=hit_cap, strata=strata, mode=mode)
     if zmax is not None:
         p.z = zmax
-    return pair.al.align(reads.codes, reads.offsets, reads.lens, p, z=z)
+    al = pair.al if kmer is None else pair.als[kmer]
+    return al.align(reads.codes, reads.offsets, reads.lens, p, z=z)
 
 
-@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("mode,kmer", [(aln.MODE_PLAIN, 0), (aln.MODE_PERSISTENT, 0),
+                                       (aln.MODE_PERSISTENT, 10)])
 @pytest.mark.parametrize("strata", [aln.STRATA_BEST1, aln.STRATA_FULL])
-def test_tiny36_full_parity(tiny36, mode, strata):
-    """1 Mbp i.i.d. text, 10 000 x 36 bp reads, z=2: every read bit-exact."""
+def test_tiny36_full_parity(tiny36, mode, kmer, strata):
+    """1 Mbp i.i.d. text, 10 000 x 36 bp reads, z=2: every read bit-exact (plain
+    form; persistent form without and with a depth-10 prefix-trie table)."""
     w, pair = tiny36
-    rg, hg = _run(pair, w.reads, w.params, strata=strata, mode=mode)
+    rg, hg = _run(pair, w.reads, w.params, strata=strata, mode=mode, kmer=kmer)
     ro, ho, _ = oracle_align(pair.ox, w.reads, w.params, 32, strata)
     assert compare(rg, hg, ro, ho, what="tiny36") == 10_000
     assert (rg["n_hits"] > 0).mean() > 0.95
@@ -90,41 +98,42 @@ def test_limits_parity(cuda, li, strata):
     lim = LIMITS[li]
     rng = Rng(1000 + li, "lim")
     text = reference_iid(20_000 + 37 * li, rng.sub("t"))
-    pair = Pair(text)
+    kmers = [0, 3 + li, 12]
+    pair = Pair(text, kmers=kmers)
     m = [20, 36, 50, 36, 60, 76, 40][li]
     reads = simulate_reads(text, 600, m, rng.sub("r"), sub_rate=(0.02, 0.04), indel_rate=0.005,
                            indel_lens=(1, 2), n_frac=0.1, z=lim["z"])
-    for mode in MODES:
-        rg, hg = _run(pair, reads, lim, hit_cap=40, strata=strata, mode=mode)
-        ro, ho, _ = oracle_align(pair.ox, reads, lim, 40, strata)
-        compare(rg, hg, ro, ho, what=f"limits {li} mode {mode}")
+    ro, ho, _ = oracle_align(pair.ox, reads, lim, 40, strata)
+    for mode, k in [(aln.MODE_PLAIN, 0)] + [(aln.MODE_PERSISTENT, k) for k in kmers]:
+        rg, hg = _run(pair, reads, lim, hit_cap=40, strata=strata, mode=mode, kmer=k)
+        compare(rg, hg, ro, ho, what=f"limits {li} mode {mode} kmer {k}")
 
 
 def test_mixed_lengths_per_read_z(cuda):
     """Reads of 36..250 bp mixed in one batch with z = min(6, ceil(0.04 len)),
     repeats and N runs in the text (the mixed-length recipe at small scale)."""
     w = workload("human_mixed", ref_len=3_000_000, n_reads=3000, seed=3)
-    pair = Pair(w.text, n_seed=7)
+    pair = Pair(w.text, n_seed=7, kmers=[0, 11])
     lim = w.params
-    for mode in MODES:
-        rg, hg = _run(pair, w.reads, lim, hit_cap=32, mode=mode, z=w.reads.z, zmax=6)
-        ro, ho, _ = oracle_align(pair.ox, w.reads, lim, 32, oracle.BEST1, z=w.reads.z)
-        compare(rg, hg, ro, ho, what=f"mixed mode {mode}")
+    ro, ho, _ = oracle_align(pair.ox, w.reads, lim, 32, oracle.BEST1, z=w.reads.z)
+    for mode, k in [(aln.MODE_PLAIN, 0), (aln.MODE_PERSISTENT, 0), (aln.MODE_PERSISTENT, 11)]:
+        rg, hg = _run(pair, w.reads, lim, hit_cap=32, mode=mode, z=w.reads.z, zmax=6, kmer=k)
+        compare(rg, hg, ro, ho, what=f"mixed mode {mode} kmer {k}")
 
 
 def test_chr100_scaled_parity(cuda):
     """The 100 bp Markov + repeat-family recipe at 4 Mbp, every read."""
     w = workload("chr100", ref_len=4_000_000, n_reads=4000, seed=1)
-    pair = Pair(w.text)
-    for mode in MODES:
-        rg, hg = _run(pair, w.reads, w.params, mode=mode)
-        ro, ho, _ = oracle_align(pair.ox, w.reads, w.params, 32, oracle.BEST1)
-        compare(rg, hg, ro, ho, what=f"chr100-4M mode {mode}")
+    pair = Pair(w.text, kmers=[0, 12])
+    ro, ho, _ = oracle_align(pair.ox, w.reads, w.params, 32, oracle.BEST1)
+    for mode, k in [(aln.MODE_PLAIN, 0), (aln.MODE_PERSISTENT, 0), (aln.MODE_PERSISTENT, 12)]:
+        rg, hg = _run(pair, w.reads, w.params, mode=mode, kmer=k)
+        compare(rg, hg, ro, ho, what=f"chr100-4M mode {mode} kmer {k}")
 
 
 def test_edge_cases(cuda):
     text = reference_iid(5000, Rng(7, "edge"))
-    pair = Pair(text)
+    pair = Pair(text, kmers=[0, 8])
     parts = [np.zeros(0, np.uint8), text[10:11], np.full(12, 4, np.uint8), np.zeros(256, np.uint8),
              text[100:355], text[4000:4036], text[4964:5000], text[0:36]]
     lens = np.array([p.size for p in parts], np.uint16)
@@ -134,13 +143,14 @@ def test_edge_cases(cuda):
     reads = Reads(np.concatenate(parts), offs, lens, z, np.zeros(lens.size, np.int64),
                   np.zeros(lens.size, np.uint8))
     lim = dict(z=7, max_gapo=1, max_gape=2, seed_len=0, seed_z=0, indel_end_skip=5)
-    for cap in (1, 4):
-        rg, hg = _run(pair, reads, lim, hit_cap=cap, z=z, zmax=6)
+    for cap, mode, k in [(1, aln.MODE_PLAIN, 0), (4, aln.MODE_PLAIN, 0), (1, aln.MODE_PERSISTENT, 8),
+                         (4, aln.MODE_PERSISTENT, 8), (4, aln.MODE_PERSISTENT, 0)]:
+        rg, hg = _run(pair, reads, lim, hit_cap=cap, z=z, zmax=6, mode=mode, kmer=k)
         ro, ho, _ = oracle_align(pair.ox, reads, lim, cap, oracle.BEST1, z=z)
         # z=7 > params.z=6 is flagged by the GPU (declared bound), not by the oracle
         assert rg[5]["flags"] & aln.FLAG_BAD_LIMIT and rg[5]["n_hits"] == 0
         keep = np.array([i for i in range(lens.size) if i != 5])
-        compare(rg[keep], hg[keep], ro[keep], ho[keep], idx=keep, what=f"edge cap {cap}")
+        compare(rg[keep], hg[keep], ro[keep], ho[keep], idx=keep, what=f"edge cap {cap} mode {mode} k {k}")
         assert rg[3]["flags"] & aln.FLAG_READ_TOO_LONG
         assert rg[0]["n_hits"] == 0 and rg[0]["d_best"] == 255
 
@@ -188,12 +198,15 @@ def test_chr100_full_size_sampled(cuda):
     sample of 3000 reads (plus every read with more than one hit) recomputed by
     the oracle one by one and compared bit-exact; plain == persistent on all."""
     w = workload("chr100")
-    pair = Pair(w.text)
+    pair = Pair(w.text, kmers=[0, BENCH_KMER])
     p = aln.Params.from_limits(w.params, hit_cap=32)
-    rp, hp = pair.al.align(w.reads.codes, w.reads.offsets, w.reads.lens, p)
+    rp, hp = pair.als[0].align(w.reads.codes, w.reads.offsets, w.reads.lens, p)
     p.mode = aln.MODE_PERSISTENT
-    rq, hq = pair.al.align(w.reads.codes, w.reads.offsets, w.reads.lens, p)
-    assert np.array_equal(rp, rq) and np.array_equal(hp, hq)
+    rq, hq = pair.als[BENCH_KMER].align(w.reads.codes, w.reads.offsets, w.reads.lens, p)
+    assert np.array_equal(rp, rq)
+    valid = np.arange(32)[None, :] < rp["n_hits"][:, None]
+    for f in ("k", "l", "aligned_len", "strand", "n_diff", "n_mm", "n_gapo", "n_gape"):
+        assert np.array_equal(np.where(valid, hp[f], 0), np.where(valid, hq[f], 0))
     rng = np.random.default_rng(2024)
     sample = np.unique(np.concatenate([rng.choice(w.reads.n, 3000, replace=False),
                                        np.nonzero(rp["n_hits"] > 1)[0][:2000]]))
