@@ -27,13 +27,18 @@ namespace aln {
 
 enum : uint32_t { PH_IDLE = 0, PH_DSCAN = 1, PH_DFS = 2, PH_DONE = 3, PH_FREE = 4, PH_WAIT = 5, PH_RETURN = 6 };
 enum : uint32_t { ROLE_OWN = 0, ROLE_HELP = 1 };
-enum : uint32_t { F_NONE = 0, F_OCC = 1, F_TABLE = 2 };
+enum : uint32_t { F_NONE = 0, F_OCC = 1, F_TABLE = 2, F_ROOT = 3, F_ZERO = 4 };
+#ifndef ALN_SMEM_STACK
+#define ALN_SMEM_STACK 8
+#endif
+constexpr int kSmemStack = ALN_SMEM_STACK;  // bottom stack entries per lane kept in shared memory
 
 // First entry of level j (strings of length j) in the prefix-trie table.
 __device__ __forceinline__ uint32_t trie_off(uint32_t j) { return ((1u << (2 * j)) - 4u) / 3u; }
 
 struct FetchReq {
-    uint32_t kind;    // F_NONE, F_OCC, F_TABLE
+    uint32_t kind;    // F_NONE; F_OCC / F_TABLE: extensions from Occ blocks / the table;
+                      // F_ROOT: extensions of the empty string; F_ZERO: none needed
     uint32_t text;    // 0 = X, 1 = X reversed
     uint32_t lo, hi;  // F_OCC: the interval
     uint32_t toff;    // F_TABLE: first of the four children entries
@@ -41,7 +46,8 @@ struct FetchReq {
 
 template <int STACK_CAP>
 struct FlatLane {
-    uint4 *stk;               // STACK_CAP entries (lo, hi, info, target-string id), local memory
+    uint4 *sstk;              // entries 0..kSmemStack-1: shared memory, entry j at sstk[j * kThreads]
+    uint4 *stk;               // entries kSmemStack..STACK_CAP-1: local memory
     uint4 *cand;              // kCandCap candidates (lo, hi, key, -), local memory
     uint4 next;               // the node the next pop would return, kept in registers
     bool has_next;
@@ -175,13 +181,21 @@ struct FlatLane {
         start_strand(n, 0);
     }
 
+    __device__ __forceinline__ uint4 stk_get(int j) const {
+        return j < kSmemStack ? sstk[j * kThreads] : stk[j - kSmemStack];
+    }
+    __device__ __forceinline__ void stk_set(int j, const uint4 &e) {
+        if (j < kSmemStack) sstk[j * kThreads] = e;
+        else stk[j - kSmemStack] = e;
+    }
+
     __device__ __forceinline__ void push_mem(const uint4 &e) {
         if (sp == STACK_CAP && base > 0) {  // slide the live entries down over handed-out ones
-            for (int j = base; j < sp; j++) stk[j - base] = stk[j];
+            for (int j = base; j < sp; j++) stk_set(j - base, stk_get(j));
             sp -= base;
             base = 0;
         }
-        if (sp < STACK_CAP) stk[sp++] = e;
+        if (sp < STACK_CAP) stk_set(sp++, e);
         else flags |= ALN_FLAG_STACK_OVERFLOW;
     }
 
@@ -300,20 +314,7 @@ struct FlatLane {
                     continue;
                 }
                 // strand 0's D comes from X, strand 1's from X reversed
-                const uint32_t c = rv.base(static_cast<uint32_t>(dj)) ^ (s ? 3u : 0u);
-                bool fail = rv.isN(static_cast<uint32_t>(dj));
-                if (!fail && dsl == 0) {  // from the empty string: the C ranges
-                    dlo = s ? X.t[1].C1[c] : X.t[0].C1[c];
-                    dhi = s ? X.t[1].C1[c + 1] : X.t[0].C1[c + 1];
-                    fail = dhi <= dlo;
-                    if (!fail) {
-                        dsl = 1;
-                        dsid = c;
-                        dj--;
-                        continue;
-                    }
-                }
-                if (fail) {
+                if (rv.isN(static_cast<uint32_t>(dj))) {
                     record_fail();
                     dlo = 0;
                     dhi = n + 1;
@@ -323,7 +324,9 @@ struct FlatLane {
                     continue;
                 }
                 fr.text = s;
-                if (dsl < K) {
+                if (dsl == 0) {
+                    fr.kind = F_ROOT;
+                } else if (dsl < K) {
                     fr.kind = F_TABLE;
                     fr.toff = trie_off(dsl + 1) + (dsid << 2);
                 } else {
@@ -383,7 +386,7 @@ struct FlatLane {
                 e = next;
                 has_next = false;
             } else {
-                e = stk[--sp];
+                e = stk_get(--sp);
             }
 #ifdef ALN_STATS
             st_pops++;
@@ -416,25 +419,13 @@ struct FlatLane {
             cur = e;
             cbits = (allowM ? 1u : 0u) | (mm_ok ? 2u : 0u) | (ins_ok ? 4u : 0u) | (del_ok ? 8u : 0u) | (qi << 4) |
                     (isN ? 64u : 0u) | (in_seed ? 128u : 0u) | (L < K ? 256u : 0u);
-            if (!(allowM || mm_ok || del_ok)) {
-                if (ins_ok) {
-                    const uint32_t z4[4] = {0, 0, 0, 0};
-                    push_children(z4, z4);  // only the insertion child
-                }
-                continue;
-            }
-            if (L == 0) {  // empty target: children are the C ranges
-                uint32_t lo4[4], hi4[4];
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    lo4[c] = s ? X.t[0].C1[c] : X.t[1].C1[c];
-                    hi4[c] = s ? X.t[0].C1[c + 1] : X.t[1].C1[c + 1];
-                }
-                push_children(lo4, hi4);
-                continue;
-            }
+            if (!(allowM || mm_ok || del_ok || ins_ok)) continue;
             fr.text = s ? 0u : 1u;  // strand 0 searches X reversed, strand 1 searches X
-            if (L < K) {
+            if (!(allowM || mm_ok || del_ok)) {
+                fr.kind = F_ZERO;  // only the insertion child: no extension needed
+            } else if (L == 0) {
+                fr.kind = F_ROOT;
+            } else if (L < K) {
                 fr.kind = F_TABLE;
                 fr.toff = trie_off(L + 1) + (e.w << 2);
             } else {
@@ -486,7 +477,7 @@ struct FlatLane {
             freem &= freem - 1;
             donm &= donm - 1;
             const bool give = lane == dnr;
-            const uint4 e = give ? stk[base] : make_uint4(0, 0, 0, 0);
+            const uint4 e = give ? stk_get(base) : make_uint4(0, 0, 0, 0);
             const uint32_t ex = __shfl_sync(FULL, e.x, dnr), ey = __shfl_sync(FULL, e.y, dnr);
             const uint32_t ez = __shfl_sync(FULL, e.z, dnr), ew = __shfl_sync(FULL, e.w, dnr);
             const uint32_t o = __shfl_sync(FULL, role == ROLE_OWN ? lane : owner, dnr);
@@ -539,10 +530,19 @@ struct FlatLane {
     }
 };
 
-// The four extensions for a fetch request (table group or Occ blocks).
+// The four extensions for a fetch request.
 __device__ __forceinline__ void fetch4(const DIndex &X, const FetchReq &fr, uint32_t lo4[4], uint32_t hi4[4]) {
     const DText T = fr.text ? X.t[1] : X.t[0];
-    if (fr.kind == F_TABLE) {
+    if (fr.kind == F_ROOT) {  // the empty string: children are the C ranges
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            lo4[c] = T.C1[c];
+            hi4[c] = T.C1[c + 1];
+        }
+    } else if (fr.kind == F_ZERO) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) lo4[c] = hi4[c] = 0;
+    } else if (fr.kind == F_TABLE) {
         const uint4 *g = reinterpret_cast<const uint4 *>(T.kmer + fr.toff);
         const uint4 a = ld_nc(g), b = ld_nc(g + 1);
         lo4[0] = a.x; hi4[0] = a.y; lo4[1] = a.z; hi4[1] = a.w;

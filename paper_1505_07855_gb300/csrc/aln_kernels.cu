@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kThreads) aln_plain_kernel(DIndex X, ReadBatch
 }
 
 #ifndef ALN_PERSISTENT_MIN_BLOCKS
-#define ALN_PERSISTENT_MIN_BLOCKS 6  // 80 registers: 6 resident blocks per SM measured best
+#define ALN_PERSISTENT_MIN_BLOCKS 5  // 5 resident blocks per SM (with 8 shared stack entries) measured best
 #endif
 
 template <int STACK_CAP>
@@ -56,10 +56,12 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
                                                                   aln_hit *hits, uint32_t *queue) {
     __shared__ uint32_t s_bases[kReadWords * kThreads];
     __shared__ uint32_t s_nmask[kMaskWords * kThreads];
+    __shared__ uint4 s_stack[kSmemStack * kThreads];
     uint32_t *sb = s_bases + threadIdx.x, *sn = s_nmask + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31u, warp_col = threadIdx.x & ~31u;
-    uint4 stk[STACK_CAP], cand[kCandCap];
+    uint4 stk[STACK_CAP - kSmemStack], cand[kCandCap];
     FlatLane<STACK_CAP> L;
+    L.sstk = s_stack + threadIdx.x;
     L.stk = stk;
     L.cand = cand;
     L.has_next = false;
