@@ -121,6 +121,72 @@ def oracle_sample(w, n_sample, threads, seed=7):
     return ox, idx, ro, ho, look, t_index, t_align
 
 
+def serving_phase(aln, dix, w, lam, seconds, seed=5):
+    """Poisson request stream on the resident index: request sizes log-uniform on
+    [1, 100000] reads, lengths uniform over 50..250 bp, z = min(6, ceil(0.04 len)),
+    errors as the tiny36 recipe; reads are cut from a pre-simulated pool."""
+    import threading
+    from synth import Rng, simulate_reads, z_for_length
+    pool_n = 400_000
+    pool = simulate_reads(w.text, pool_n, np.arange(50, 251), Rng(seed, "serve-pool"), sub_rate=(0.01, 0.01),
+                          indel_rate=0.0005, indel_lens=(1,), n_frac=0.02, z_of_len=z_for_length)
+    rng = np.random.default_rng(seed)
+    params = aln.Params(z=6, max_gapo=w.params["max_gapo"], max_gape=w.params["max_gape"],
+                        seed_len=0, seed_z=0, indel_end_skip=5, hit_cap=8, mode=aln.MODE_PERSISTENT)
+    srv = aln.Server(dix, params, n_slots=3, max_batch_reads=1 << 19, coalesce_us=500)
+    done, lock = [], threading.Lock()
+    pending = []
+    stop = threading.Event()
+    offered = [0]
+
+    def poller():
+        while not stop.is_set() or pending:
+            with lock:
+                items = list(pending)
+            for it in items:
+                r = srv.poll(it[0], it[1], wait_ms=1)
+                if r is not None:
+                    with lock:
+                        pending.remove(it)
+                        done.append(r[2])
+            if not items:
+                stop.wait(0.001)
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t0 = time.time()
+    t_next = t0
+    while True:
+        t_next += rng.exponential(1.0 / lam)
+        if t_next - t0 > seconds:
+            break
+        delay = t_next - time.time()
+        if delay > 0:
+            time.sleep(delay)
+        n = int(np.exp(rng.uniform(0, np.log(100_000))))
+        a = int(rng.integers(0, pool_n - n))
+        lens = pool.lens[a:a + n]
+        offs = pool.offsets[a:a + n] - pool.offsets[a]
+        codes = pool.codes[int(pool.offsets[a]):int(pool.offsets[a + n - 1]) + int(lens[-1])]
+        rid = srv.submit(codes, offs, lens, pool.z[a:a + n])
+        offered[0] += n
+        with lock:
+            pending.append((rid, n))
+    stop.set()
+    th.join(timeout=300)
+    elapsed = time.time() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(done)
+    return {"lambda_req_per_s": lam, "seconds": seconds, "requests": int(lat.size),
+            "reads_per_s": st["reads_done"] / elapsed, "offered_reads_per_s": offered[0] / seconds,
+            "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+            "p95_ms": float(np.percentile(lat, 95)) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+            "batches": st["batches"], "slots": st["n_slots"],
+            "text": "the 100 Mbp bench text stands in for the 3.1 Gbp one"}
+
+
 def run_reference(args):
     """CPU oracle arm: each step aligns a bounded seeded sample on all host cores."""
     ws, rank, _ = _dist()
@@ -325,6 +391,55 @@ def run_gpu(args):
                                 "sample": f"{sel.size} seeded reads of the {n}-read batch, "
                                           f"oracle index build ({t_index:.1f} s) not timed"}
         line["parity"] = {"sampled_reads": int(sel.size), "bit_exact": bool(ok)}
+    # SA walk of every hit of the timed run (positions of hits of width <= 16)
+    rg, hg = out["persistent"]
+    valid = np.arange(hit_cap)[None, :] < rg["n_hits"][:, None]
+    hits_all = hg[valid]
+    dh = torch.from_numpy(hits_all.view(np.uint8).copy()).to(dev)
+    pos = torch.empty(max(1, hits_all.size * 16), dtype=torch.int64, device=dev)
+    npos = torch.empty(max(1, hits_all.size), dtype=torch.int32, device=dev)
+    sa_ms = []
+    with torch.cuda.stream(stream):
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dix.sa_to_pos(dh, hits_all.size, 16, pos, npos, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= args.warmup:
+                sa_ms.append(e0.elapsed_time(e1))
+    np_h = npos.cpu().numpy().view(np.uint32)[:hits_all.size]
+    n_pos = int(np_h[np_h <= 16].sum())
+    line["sa_to_pos"] = {"hits": int(hits_all.size), "positions": n_pos, "ms": float(np.mean(sa_ms)),
+                         "positions_per_s": n_pos / (np.mean(sa_ms) / 1000)}
+    if rank == 0 and not args.no_oracle:
+        # positions of the sampled reads' hits against the oracle's full suffix arrays
+        sel_hits = hg[sel][np.arange(hit_cap)[None, :] < rg[sel]["n_hits"][:, None]]
+        pos_h = pos.cpu().numpy().view(np.uint64)[:hits_all.size * 16].reshape(-1, 16)
+        idx_valid = np.nonzero(valid.reshape(-1))[0]
+        row_of = np.full(valid.size, -1, np.int64)
+        row_of[idx_valid] = np.arange(idx_valid.size)
+        flat_sel = (sel[:, None] * hit_cap + np.arange(hit_cap)[None, :])[np.arange(hit_cap)[None, :] < rg[sel]["n_hits"][:, None]]
+        rows = row_of[flat_sel]
+        import oracle
+        oh = np.zeros(sel_hits.size, oracle.HIT_DTYPE)
+        for f in ("k", "l", "aligned_len", "strand"):
+            oh[f] = sel_hits[f]
+        opos, onpos = ox.positions(oh, 16)
+        okp = True
+        for j, rrow in enumerate(rows):
+            w_ = int(sel_hits[j]["l"]) - int(sel_hits[j]["k"]) + 1
+            if w_ <= 16:
+                okp = okp and int(np_h[rrow]) == int(onpos[j]) and np.array_equal(pos_h[rrow, :w_], opos[j, :w_])
+            else:
+                okp = okp and int(np_h[rrow]) == 0xFFFFFFFF
+        line["parity"]["positions_bit_exact"] = bool(okp)
+        line["parity"]["positions_hits_checked"] = int(sel_hits.size)
+    if args.serve_seconds > 0:
+        line["serving"] = serving_phase(aln, dix, w, args.serve_lambda, args.serve_seconds)
+        line["p99_ms"] = line["serving"]["p99_ms"]
     line["wall_s"] = time.time() - t_all
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -345,6 +460,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2000)
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--reads", type=int, default=0, help="use only the first N reads (profiling runs)")
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-lambda", type=float, default=100.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -50,6 +50,7 @@ extern "C" {
 #define ALN_ELIMIT (-4)    /* a bounded loop reached its iteration limit */
 #define ALN_EOVERFLOW (-5) /* a caller-provided buffer is too small */
 #define ALN_EIO (-6)       /* file could not be read or written, or is malformed */
+#define ALN_EAGAIN (-7)    /* not finished yet (aln_server_poll within its wait) */
 
 /* ---------------------------------------------------------------- limits */
 #define ALN_MAX_READ_LEN 255 /* longer reads get ALN_FLAG_READ_TOO_LONG and no hits */
@@ -217,6 +218,55 @@ int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
  * memory; max_width 1..64.  Asynchronous on stream. */
 int sa_to_pos(const fm_dindex *idx, const aln_hit *hits, uint32_t n_hits, uint32_t max_width,
               uint64_t *pos_out, uint32_t *n_pos_out, void *stream);
+
+/* ---------------------------------------------------------------- serving
+ *
+ * Continuous batching on a resident index.  Requests (host reads, copied at
+ * submit) are queued; a dispatcher thread keeps up to n_slots batches in flight,
+ * each a fixed set of device buffers with pinned staging and its own stream,
+ * sized at creation and admitted only within the device-memory budget.  A free
+ * slot takes reads from the oldest requests (a large request is split across
+ * batches) and runs copy-in, one persistent aln_search and copy-out; requests
+ * arriving while batches run join the next free slot, so batches overlap on the
+ * device.  A read's result depends only on the read, the limits and the index,
+ * so it is identical alone and in any mix.  Latency = completion - submit. */
+typedef struct aln_server aln_server;
+
+typedef struct {
+    int32_t device;             /* CUDA ordinal of the index */
+    uint32_t n_slots;           /* batches in flight, 1..16 (reduced to what the budget holds) */
+    uint32_t max_batch_reads;   /* reads per batch */
+    uint64_t max_batch_bases;   /* bases per batch (>= max_batch_reads) */
+    uint64_t device_mem_budget; /* bytes for all slots; 0 = half of the free device memory */
+    uint32_t coalesce_us;       /* with batches already running, let a partly filled batch wait
+                                   this long for more requests; 0 = launch at once */
+    uint32_t reserved;
+    aln_params params;          /* limits (mode is forced to ALN_MODE_PERSISTENT); params.z also
+                                   bounds the per-read z of requests */
+} aln_server_config;
+
+typedef struct {
+    uint64_t requests_done, reads_done, batches, queued_reads;
+    double p50_ms, p95_ms, p99_ms; /* over every completed request since creation */
+    double seconds;                /* since creation */
+    uint32_t n_slots, reserved;
+} aln_server_stats_t;
+
+/* Start the dispatcher; allocates the slots.  ALN_ENOMEM if no slot fits. */
+int aln_server_create(const fm_dindex *idx, const aln_server_config *cfg, aln_server **out);
+/* Queue a request: reads as codes 0..4 (read r at codes[code_offset[r]], len[r]
+ * bases), per-read z (NULL = params.z).  The reads are copied; the caller's
+ * buffers are free on return.  *request_id identifies it for aln_server_poll. */
+int aln_server_submit(aln_server *s, const uint8_t *codes, const uint64_t *code_offset, const uint16_t *len,
+                      const uint8_t *z, uint32_t n_reads, uint64_t *request_id);
+/* Wait up to wait_ms for a request.  On completion copies n_reads results and
+ * n_reads * hit_cap hits (host memory, either may be NULL), the latency, forgets
+ * the request and returns ALN_OK; ALN_EAGAIN if not finished in time. */
+int aln_server_poll(aln_server *s, uint64_t request_id, int wait_ms, aln_read_result *res_out,
+                    aln_hit *hits_out, double *latency_ms);
+int aln_server_stats(aln_server *s, aln_server_stats_t *out);
+/* Stop the dispatcher (batches in flight finish first) and free everything. */
+void aln_server_destroy(aln_server *s);
 
 /* ---------------------------------------------------------------- no-allocation variant
  *

@@ -150,9 +150,11 @@ class Params:
 
     @classmethod
     def from_limits(cls, lim: dict, **kw) -> "Params":
-        return cls(z=lim["z"], max_gapo=lim["max_gapo"], max_gape=lim["max_gape"],
-                   seed_len=lim["seed_len"], seed_z=lim["seed_z"],
-                   indel_end_skip=lim["indel_end_skip"], **kw)
+        """Params from a limits dict; keyword arguments override its entries."""
+        d = dict(z=lim["z"], max_gapo=lim["max_gapo"], max_gape=lim["max_gape"],
+                 seed_len=lim["seed_len"], seed_z=lim["seed_z"], indel_end_skip=lim["indel_end_skip"])
+        d.update(kw)
+        return cls(**d)
 
 
 def pack_reads(codes: np.ndarray, offsets: np.ndarray, lens: np.ndarray):
@@ -227,3 +229,58 @@ class Aligner:
         t.cuda.synchronize(self.dev)
         return (pos.cpu().numpy().view(np.uint64)[:n * max_width].reshape(n, max_width),
                 npos.cpu().numpy().view(np.uint32)[:n])
+
+
+class Server:
+    """Continuous-batching request loop on a resident index (aln_server_*)."""
+
+    def __init__(self, dindex: DeviceIndex, params: Params, n_slots: int = 3,
+                 max_batch_reads: int = 1 << 18, max_batch_bases: int = 0, device_mem_budget: int = 0,
+                 coalesce_us: int = 200):
+        self.dix = dindex
+        self.params = params
+        cfg = _lib.aln_server_config()
+        cfg.device = dindex.device
+        cfg.n_slots = n_slots
+        cfg.max_batch_reads = max_batch_reads
+        cfg.max_batch_bases = max_batch_bases or max_batch_reads * 256
+        cfg.device_mem_budget = device_mem_budget
+        cfg.coalesce_us = coalesce_us
+        cfg.params = params.c()
+        out = ctypes.c_void_p()
+        check(lib().aln_server_create(dindex._h, ctypes.byref(cfg), ctypes.byref(out)), "aln_server_create")
+        self._h = out
+
+    def submit(self, codes, offsets, lens, z=None) -> int:
+        codes = np.ascontiguousarray(codes, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        lens = np.ascontiguousarray(lens, dtype=np.uint16)
+        zz = None if z is None else np.ascontiguousarray(z, dtype=np.uint8)
+        rid = ctypes.c_uint64()
+        check(lib().aln_server_submit(self._h, _ptr(codes), _ptr(offsets), _ptr(lens), _ptr(zz), lens.size,
+                                      ctypes.byref(rid)), "aln_server_submit")
+        return rid.value
+
+    def poll(self, rid: int, n_reads: int, wait_ms: int = 60000):
+        """Results of a finished request as (res, hits, latency_ms), or None if not done."""
+        res = np.zeros(max(1, n_reads), RES_DTYPE)
+        hits = np.zeros(max(1, n_reads * self.params.hit_cap), HIT_DTYPE)
+        lat = ctypes.c_double()
+        rc = lib().aln_server_poll(self._h, rid, wait_ms, _ptr(res), _ptr(hits), ctypes.byref(lat))
+        if rc == _lib.ALN_EAGAIN:
+            return None
+        check(rc, "aln_server_poll")
+        return res[:n_reads], hits[:n_reads * self.params.hit_cap].reshape(n_reads, self.params.hit_cap), lat.value
+
+    def stats(self) -> dict:
+        st = _lib.aln_server_stats_t()
+        check(lib().aln_server_stats(self._h, ctypes.byref(st)), "aln_server_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().aln_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -13,7 +13,8 @@ from . import build as _build
 
 ALN_OK = 0
 STATUS = {0: "ALN_OK", -1: "ALN_EINVAL", -2: "ALN_ENOMEM", -3: "ALN_EDEVICE", -4: "ALN_ELIMIT",
-          -5: "ALN_EOVERFLOW", -6: "ALN_EIO"}
+          -5: "ALN_EOVERFLOW", -6: "ALN_EIO", -7: "ALN_EAGAIN"}
+ALN_EAGAIN = -7
 MAX_READ_LEN = 255
 MAX_Z = 7
 MAX_HIT_CAP = 255
@@ -69,8 +70,23 @@ class aln_result(ctypes.Structure):
     _fields_ = [("reads", ctypes.c_void_p), ("hits", ctypes.c_void_p)]
 
 
+class aln_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("n_slots", ctypes.c_uint32),
+                ("max_batch_reads", ctypes.c_uint32), ("max_batch_bases", ctypes.c_uint64),
+                ("device_mem_budget", ctypes.c_uint64), ("coalesce_us", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("params", aln_params)]
+
+
+class aln_server_stats_t(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_uint64), ("reads_done", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("queued_reads", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p95_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("n_slots", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 assert ctypes.sizeof(aln_params) == 16 and ctypes.sizeof(fm_build_opts) == 24
 assert ctypes.sizeof(fm_index_info_t) == 120
+assert ctypes.sizeof(aln_server_config) == 56 and ctypes.sizeof(aln_server_stats_t) == 72
 
 # name -> (restype, argtypes); the exported ABI
 P, u8p = ctypes.c_void_p, ctypes.c_void_p
@@ -89,6 +105,11 @@ SIGNATURES = {
     "aln_search_noalloc": (ctypes.c_int, [P, ctypes.POINTER(aln_batch), ctypes.c_uint32,
                                           ctypes.POINTER(aln_params), ctypes.POINTER(aln_result), P]),
     "aln_pack_reads": (ctypes.c_int, [P, P, P, ctypes.c_uint32, P, P, P]),
+    "aln_server_create": (ctypes.c_int, [P, ctypes.POINTER(aln_server_config), ctypes.POINTER(P)]),
+    "aln_server_submit": (ctypes.c_int, [P, P, P, P, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]),
+    "aln_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_double)]),
+    "aln_server_stats": (ctypes.c_int, [P, ctypes.POINTER(aln_server_stats_t)]),
+    "aln_server_destroy": (None, [P]),
     "aln_last_error": (ctypes.c_char_p, []),
     "aln_version": (ctypes.c_int, []),
 }

@@ -18,7 +18,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["aln_kernels.cu", "aln_capi.cu"]
-CPP_SOURCES = ["index_build.cpp"]
+CPP_SOURCES = ["index_build.cpp", "aln_server.cpp"]
 HEADERS = ["aln_device.cuh", "aln_search.cuh", "aln_internal.h"]
 
 

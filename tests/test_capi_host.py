@@ -182,3 +182,14 @@ def test_pack_reads_layout():
             if c < 4:
                 assert b == c
             j += 1
+
+
+def test_server_argument_errors():
+    L = aln.lib()
+    cfg = aln._lib.aln_server_config()
+    out = ctypes.c_void_p()
+    assert L.aln_server_create(None, ctypes.byref(cfg), ctypes.byref(out)) == -1
+    rid = ctypes.c_uint64()
+    assert L.aln_server_submit(None, None, None, None, None, 0, ctypes.byref(rid)) == -1
+    assert L.aln_server_poll(None, 1, 0, None, None, None) == -1
+    L.aln_server_destroy(None)
