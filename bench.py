@@ -129,7 +129,8 @@ def serving_phase(aln, dix, w, lam, seconds, seed=5):
     from synth import Rng, simulate_reads, z_for_length
     pool_n = 400_000
     pool = simulate_reads(w.text, pool_n, np.arange(50, 251), Rng(seed, "serve-pool"), sub_rate=(0.01, 0.01),
-                          indel_rate=0.0005, indel_lens=(1,), n_frac=0.02, z_of_len=z_for_length)
+                          indel_rate=0.0005, indel_lens=(1,), n_frac=0.02, z_of_len=z_for_length,
+                          nmask=w.nmask)
     rng = np.random.default_rng(seed)
     params = aln.Params(z=6, max_gapo=w.params["max_gapo"], max_gape=w.params["max_gape"],
                         seed_len=0, seed_z=0, indel_end_skip=5, hit_cap=8, mode=aln.MODE_PERSISTENT)
@@ -187,6 +188,63 @@ def serving_phase(aln, dix, w, lam, seconds, seed=5):
             "text": "the 100 Mbp bench text stands in for the 3.1 Gbp one"}
 
 
+def _levenshtein(a, b):
+    """Edit distance with an N (4) in the read matching nothing."""
+    prev = np.arange(b.size + 1)
+    for i in range(1, a.size + 1):
+        cur = np.empty_like(prev)
+        cur[0] = i
+        sub = prev[:-1] + ((b != a[i - 1]) | (a[i - 1] == 4))
+        cur[1:] = np.minimum(sub, prev[1:] + 1)
+        for j in range(1, b.size + 1):  # insertion chain along the row
+            if cur[j - 1] + 1 < cur[j]:
+                cur[j] = cur[j - 1] + 1
+        prev = cur
+    return int(prev[-1])
+
+
+def property_checks(w, outp, pos, npos, hit_cap, n_hits, valid, n_sample=400, seed=3):
+    """Checks that hold at any size (used where the oracle's index is too large
+    to build): every sampled hit's target, at each reported position, lies
+    within the hit's difference count of the read (edit distance, the text's N
+    replaced as the index replaced it), and the simulated origin of each
+    sampled read is among its hits' positions (recall)."""
+    from synth import mix64, revcomp_codes
+    rg, hg = outp
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(rg.size, min(n_sample, rg.size), replace=False))
+    pos_h = pos.cpu().numpy().view(np.uint64)[:n_hits * 16].reshape(-1, 16)
+    np_h = npos.cpu().numpy().view(np.uint32)[:n_hits]
+    row_of = np.full(valid.size, -1, np.int64)
+    iv = np.nonzero(valid.reshape(-1))[0]
+    row_of[iv] = np.arange(iv.size)
+    text = w.text
+    sound = checked = found = eligible = 0
+    for r in sel:
+        read = w.reads.read(int(r))
+        hit_pos = set()
+        for j in range(int(rg[r]["n_hits"])):
+            h = hg[r, j]
+            row = row_of[r * hit_cap + j]
+            if np_h[row] > 16:
+                continue
+            q = read if h["strand"] == 0 else revcomp_codes(read)
+            for p in pos_h[row, :np_h[row]]:
+                p = int(p)
+                hit_pos.add((p, int(h["strand"])))
+                T = text[p:p + int(h["aligned_len"])].copy()
+                nm = T == 4
+                if nm.any():
+                    T[nm] = (mix64(np.uint64(0) ^ (np.nonzero(nm)[0] + p).astype(np.uint64)) & np.uint64(3)).astype(np.uint8)
+                checked += 1
+                sound += _levenshtein(q, T) <= int(h["n_diff"])
+        eligible += 1
+        found += (int(w.reads.true_pos[r]), int(w.reads.true_strand[r])) in hit_pos
+    return {"kind": "properties (oracle index not built at this size)", "sampled_reads": int(sel.size),
+            "hits_checked": checked, "hits_sound": sound, "all_sound": sound == checked,
+            "origin_recall": found / max(1, eligible)}
+
+
 def run_reference(args):
     """CPU oracle arm: each step aligns a bounded seeded sample on all host cores."""
     ws, rank, _ = _dist()
@@ -237,11 +295,18 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     t_all = time.time()
-    w = workload(args.workload)
-    if args.reads:
-        w.reads = w.reads.subset(np.arange(min(args.reads, w.reads.n)))
+    big = args.workload in ("human_mixed", "human_pairs")
+    n_req = args.reads or (1_000_000 if big else None)
+    if args.workload == "human_pairs" and n_req:
+        n_req //= 2  # pairs: two reads each, both mates in one batch
+    t_gen = time.time()
+    w = workload(args.workload, ref_len=args.ref_len or None, n_reads=n_req)
+    t_gen = time.time() - t_gen
+    if args.reads and w.reads.n > args.reads:
+        w.reads = w.reads.subset(np.arange(args.reads))
     lim = w.params
     n = w.reads.n
+    per_read_z = args.workload == "human_mixed"
     # index: rank 0 builds and saves, the other replicas load the image
     t0 = time.time()
     if ws > 1:
@@ -261,12 +326,14 @@ def run_gpu(args):
     d = {"bases": torch.from_numpy(bases.view(np.int32)).to(dev),
          "nmask": torch.from_numpy(nmask.view(np.int32)).to(dev),
          "offsets": torch.from_numpy(offs.view(np.int64)).to(dev),
-         "lens": torch.from_numpy(lens.view(np.int16)).to(dev), "z": None, "n": n}
+         "lens": torch.from_numpy(lens.view(np.int16)).to(dev),
+         "z": torch.from_numpy(np.ascontiguousarray(w.reads.z)).to(dev) if per_read_z else None, "n": n}
     hit_cap = 32
     res, hits = al.outputs(n, hit_cap)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     modes = {"persistent": aln.MODE_PERSISTENT, "plain": aln.MODE_PLAIN}
-    params = {k: aln.Params.from_limits(lim, hit_cap=hit_cap, mode=m, blocks_per_sm=args.blocks_per_sm)
+    params = {k: aln.Params.from_limits(lim, hit_cap=hit_cap, mode=m, blocks_per_sm=args.blocks_per_sm,
+                                        work_limit=args.work_limit, **({"z": 6} if per_read_z else {}))
               for k, m in modes.items()}
 
     def step(mode):
@@ -307,8 +374,21 @@ def run_gpu(args):
         t = torch.tensor([ms_head, ms_plain], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_head, ms_plain = float(t[0]), float(t[1])
-    same = bool(np.array_equal(out["plain"][0], out["persistent"][0]) and
-                np.array_equal(out["plain"][1], out["persistent"][1]))
+    rp, hp = out["plain"]
+    rq, hq = out["persistent"]
+    inc = ((rp["flags"] | rq["flags"]) & aln.FLAG_INCOMPLETE) != 0
+    okr = ~inc
+    vmask = np.arange(hit_cap)[None, :] < rq["n_hits"][:, None]
+    same = bool(np.array_equal(rp[okr], rq[okr]) and all(
+        np.array_equal(np.where(vmask, hp[f], 0)[okr], np.where(vmask, hq[f], 0)[okr])
+        for f in ("k", "l", "aligned_len", "strand", "n_diff", "n_mm", "n_gapo", "n_gape")))
+    fl = rq["flags"]
+    flag_counts = {"incomplete": int(((fl & aln.FLAG_INCOMPLETE) != 0).sum()),
+                   "work_limit": int(((fl & aln.FLAG_WORK_LIMIT) != 0).sum()),
+                   "cand_overflow": int(((fl & aln.FLAG_CAND_OVERFLOW) != 0).sum()),
+                   "stack_overflow": int(((fl & aln.FLAG_STACK_OVERFLOW) != 0).sum()),
+                   "hit_overflow": int(((fl & aln.FLAG_HIT_OVERFLOW) != 0).sum()),
+                   "no_hit": int((rq["n_hits"] == 0).sum())}
 
     # end to end through the public API with host buffers (pinned), copies timed
     h_bases = torch.from_numpy(bases.view(np.int32)).pin_memory()
@@ -344,18 +424,21 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_head, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload, "ref_bp": int(w.text.size), "reads_per_step": n,
-                   "read_len": 100, "z": lim["z"], "seed": [lim["seed_len"], lim["seed_z"]],
+                   "read_len": "36-250 mixed" if per_read_z else 100,
+                   "z": "min(6, ceil(0.04 len))" if per_read_z else lim["z"], "seed": [lim["seed_len"], lim["seed_z"]],
                    "strata": "BEST1", "mode": "persistent", "l2": "flushed (512 MiB write) before every step",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single"},
         "plain": {"value": ws * n / (ms_plain / 1000), "ms_per_step": ms_plain,
-                  "bit_identical_to_persistent": same},
+                  "bit_identical_to_persistent_on_complete_reads": same},
+        "flags": flag_counts,
         "gpu_launches": args.steps,
         "e2e": {"value": e2e_v, "unit": "reads/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
-        "build_s": t_build,
+        "build_s": t_build, "gen_s": t_gen,
     }
-    if rank == 0 and not args.no_oracle:
+    use_oracle = rank == 0 and not args.no_oracle and w.text.size <= args.oracle_max_bp
+    if use_oracle:
         import oracle
         threads = oracle.default_threads()
         # size the sample to ~15 s of oracle search on all host cores
@@ -414,7 +497,9 @@ def run_gpu(args):
     n_pos = int(np_h[np_h <= 16].sum())
     line["sa_to_pos"] = {"hits": int(hits_all.size), "positions": n_pos, "ms": float(np.mean(sa_ms)),
                          "positions_per_s": n_pos / (np.mean(sa_ms) / 1000)}
-    if rank == 0 and not args.no_oracle:
+    if not use_oracle and rank == 0 and not args.no_oracle:
+        line["parity"] = property_checks(w, out["persistent"], pos, npos, hit_cap, hits_all.size, valid)
+    if use_oracle:
         # positions of the sampled reads' hits against the oracle's full suffix arrays
         sel_hits = hg[sel][np.arange(hit_cap)[None, :] < rg[sel]["n_hits"][:, None]]
         pos_h = pos.cpu().numpy().view(np.uint64)[:hits_all.size * 16].reshape(-1, 16)
@@ -453,9 +538,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="chr100", choices=["chr100", "tiny36"])
+    ap.add_argument("--workload", default="chr100", choices=["chr100", "tiny36", "human_mixed", "human_pairs"])
+    ap.add_argument("--ref-len", type=int, default=0, help="reference length (default: the workload's)")
+    ap.add_argument("--oracle-max-bp", type=int, default=400_000_000,
+                    help="above this text size the oracle is not built; sampled hits are checked by properties")
     ap.add_argument("--kmer-k", type=int, default=10)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--work-limit", type=int, default=0, help="node expansions per read (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=2000)
     ap.add_argument("--no-oracle", action="store_true")

@@ -19,7 +19,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["aln_kernels.cu", "aln_capi.cu"]
 CPP_SOURCES = ["index_build.cpp", "aln_server.cpp"]
-HEADERS = ["aln_device.cuh", "aln_search.cuh", "aln_internal.h"]
+HEADERS = ["aln_device.cuh", "aln_search.cuh", "aln_flat.cuh", "aln_internal.h"]
 
 
 def _newer(target: str, deps: list[str]) -> bool:

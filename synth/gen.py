@@ -262,6 +262,15 @@ class Reads:
                      np.concatenate([r.true_strand for r in items]))
 
 
+def _mask_prefix(nmask):
+    """Prefix counts of an N mask (uint32: texts are < 2^32 bases)."""
+    if nmask is None:
+        return None
+    cs = np.zeros(nmask.size + 1, dtype=np.uint32)
+    np.cumsum(nmask, out=cs[1:], dtype=np.uint32)
+    return cs
+
+
 def _clean_starts(rng: Rng, n_reads: int, lens: np.ndarray, pad: int, n: int, nmask_cs) -> np.ndarray:
     """Uniform anchors s0 in [pad, n - len - pad] whose padded span
     [s0 - pad, s0 + len + pad) avoids N runs (resampled with fresh counters)."""
@@ -271,7 +280,8 @@ def _clean_starts(rng: Rng, n_reads: int, lens: np.ndarray, pad: int, n: int, nm
     if nmask_cs is None:
         return starts
     def bad_of(s, L):
-        return (nmask_cs[np.minimum(n, s + L + pad)] - nmask_cs[np.maximum(0, s - pad)]) > 0
+        hi = nmask_cs[np.minimum(n, s + L + pad)].astype(np.int64)
+        return (hi - nmask_cs[np.maximum(0, s - pad)].astype(np.int64)) > 0
     bad = bad_of(starts, lens)
     attempt = 1
     while bad.any():
@@ -313,10 +323,7 @@ def simulate_reads(ref: np.ndarray, n_reads: int, lengths, rng: Rng, *,
     max_indel = max(indel_lens) if indel_rate > 0 else 0
     pad = 4 * max_indel + 8
     if starts is None:
-        nmask_cs = None
-        if nmask is not None:
-            nmask_cs = np.zeros(n + 1, dtype=np.int64)
-            np.cumsum(nmask, out=nmask_cs[1:])
+        nmask_cs = _mask_prefix(nmask)
         starts = _clean_starts(rng.sub("start"), n_reads, lens, pad, n, nmask_cs)
     starts = np.asarray(starts, dtype=np.int64)
     if rev is None:
@@ -354,7 +361,8 @@ def simulate_reads(ref: np.ndarray, n_reads: int, lengths, rng: Rng, *,
         pos = np.where(rv[:, None] == 1, anchor[:, None] - jj[None, :], st[:, None] + jj[None, :])
         pos = np.clip(pos, 0, n - 1)
         win = ref[pos]
-        win = np.where(rv[:, None] == 1, 3 - win, win).astype(np.uint8)
+        comp = np.where(win < 4, 3 - win.astype(np.int16), 4).astype(np.uint8)  # N stays N
+        win = np.where(rv[:, None] == 1, comp, win).astype(np.uint8)
         tp = st.copy()
         for r in np.nonzero(has_indel)[0]:
             gi = c0 + int(r)
@@ -382,7 +390,11 @@ def simulate_reads(ref: np.ndarray, n_reads: int, lengths, rng: Rng, *,
                         p += ln
                 if len(out) >= Lr:
                     break
-                out.append(3 - int(ref[a0 - p]) if rv[r] else int(ref[s0 + p]))
+                if rv[r]:
+                    b = int(ref[a0 - p])
+                    out.append(3 - b if b < 4 else 4)
+                else:
+                    out.append(int(ref[s0 + p]))
                 p += 1
                 j += 1
             win[r, :Lr] = np.asarray(out[:Lr], dtype=np.uint8)
@@ -423,10 +435,7 @@ def simulate_pairs(ref: np.ndarray, n_pairs: int, length: int, rng: Rng, *,
     frag = np.maximum(frag, max(frag_min, length))
     max_indel = max(kw.get("indel_lens", (1,))) if kw.get("indel_rate", 0.0005) > 0 else 0
     pad = 4 * max_indel + 8
-    nmask_cs = None
-    if nmask is not None:
-        nmask_cs = np.zeros(n + 1, dtype=np.int64)
-        np.cumsum(nmask, out=nmask_cs[1:])
+    nmask_cs = _mask_prefix(nmask)
     fstart = _clean_starts(rng.sub("fstart"), n_pairs, frag, pad, n, nmask_cs)
     flip = (rng.sub("forient").u64(n_pairs) & np.uint64(1)).astype(bool)
     chim = Rng.to_unit(rng.sub("chim").u64(n_pairs)) < chimeric
