@@ -29,6 +29,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "reads/s bit-exact vs oracle (batched vs plain, 1 GB300); % HBM roofline; p99 ms"
 BYTES_PER_LOOKUP = 64
+# DRAM bytes (read + write) of aln_persistent_kernel from one ncu capture of the
+# chr100 workload (300 000 reads, scaled per read; profiles/aln_persistent_chr100.md).
+# Used only while the kernel sources hash to the value they had at capture time.
+TRAFFIC_CAPTURE = {"src_sha256_16": "4fd75af48dd661a8", "workload": "chr100", "dram_bytes_per_read": 23448.0}
+
+
+def _src_hash() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1505_07855_gb300", "csrc", "*")))
+    for f in files + [os.path.join(ROOT, "include", "aln_gb300.h")]:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -336,8 +352,22 @@ def run_gpu(args):
                                         work_limit=args.work_limit, **({"z": 6} if per_read_z else {}))
               for k, m in modes.items()}
 
+    tuned_ms = None
+    if args.autotune:
+        ns = min(n, 100_000)
+        dsub = dict(d)
+        dsub["n"] = ns
+        params["persistent"], tuned_ms = al.autotune(dsub, params["persistent"], res, hits, stream)
+    graph = None
+    if args.graph:
+        with torch.cuda.stream(stream):
+            graph = al.capture(d, params["persistent"], res, hits)
+
     def step(mode):
-        al.search_device(d, params[mode], res, hits, stream)
+        if graph is not None and mode == "persistent":
+            graph.replay()
+        else:
+            al.search_device(d, params[mode], res, hits, stream)
 
     with torch.cuda.stream(stream):
         for mode in modes:
@@ -431,6 +461,8 @@ def run_gpu(args):
         "plain": {"value": ws * n / (ms_plain / 1000), "ms_per_step": ms_plain,
                   "bit_identical_to_persistent_on_complete_reads": same},
         "flags": flag_counts,
+        "schedule": {"blocks_per_sm": params["persistent"].blocks_per_sm or "max",
+                     "autotune_ms": tuned_ms, "graph_replay": bool(graph is not None)},
         "gpu_launches": args.steps,
         "e2e": {"value": e2e_v, "unit": "reads/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -466,8 +498,11 @@ def run_gpu(args):
         alg_bytes = lookups_per_read * BYTES_PER_LOOKUP * n
         peak, src = _peaks()
         achieved = alg_bytes / (ms_head / 1000) / 1e9
+        traffic = None
+        if args.workload == TRAFFIC_CAPTURE["workload"] and _src_hash() == TRAFFIC_CAPTURE["src_sha256_16"]:
+            traffic = TRAFFIC_CAPTURE["dram_bytes_per_read"] * n
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "traffic": None, "peak_source": src,
+                            "frac": achieved / peak, "traffic": traffic, "peak_source": src,
                             "bytes_per_read": lookups_per_read * BYTES_PER_LOOKUP,
                             "occ_lookups_per_s": lookups_per_read * n / (ms_head / 1000)}
         line["cpu_baseline"] = {"value": cpu_v, "unit": "reads/s", "cores": threads, "kind": "oracle",
@@ -545,6 +580,8 @@ def main():
     ap.add_argument("--kmer-k", type=int, default=10)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--work-limit", type=int, default=0, help="node expansions per read (0 = library default)")
+    ap.add_argument("--autotune", action="store_true", help="choose blocks per SM with aln_autotune first")
+    ap.add_argument("--graph", action="store_true", help="time the persistent form as CUDA-graph replays")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=2000)
     ap.add_argument("--no-oracle", action="store_true")

@@ -204,6 +204,15 @@ typedef struct {
 int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
                const aln_params *params, aln_result *out, void *stream);
 
+/* Autotuner for the persistent form: times aln_search of a sample batch (device
+ * memory, laid out as for aln_search; scratch receives its results) once for
+ * every resident-blocks-per-SM value from 1 to what fits, after one warm-up
+ * run, and writes the fastest into params->blocks_per_sm (its time in *best_ms,
+ * may be NULL).  The remaining fields of params are used as given.  Blocks on
+ * stream.  ALN_EINVAL for an empty sample. */
+int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint32_t n_reads, aln_params *params,
+                 aln_result *scratch, void *stream, float *best_ms);
+
 #define ALN_POS_TOO_WIDE 0xFFFFFFFFu /* n_pos_out value: hit wider than max_width */
 #define ALN_POS_WALK_LIMIT 0xFFFFFFFEu /* n_pos_out value: an LF walk exceeded its bound */
 

@@ -206,6 +206,33 @@ class Aligner:
         self.dix.search(d["bases"], d["nmask"], d["offsets"], d["lens"], d["z"], d["n"], params,
                         res, hits, stream)
 
+    def autotune(self, d, params: Params, res, hits, stream=None) -> tuple:
+        """aln_autotune on an uploaded sample: returns (params with the fastest
+        blocks_per_sm, its time in ms)."""
+        b = _lib.aln_batch(_ptr(d["bases"]), _ptr(d["nmask"]), _ptr(d["offsets"]), _ptr(d["lens"]), _ptr(d["z"]))
+        r = _lib.aln_result(_ptr(res), _ptr(hits))
+        p = params.c()
+        ms = ctypes.c_float()
+        check(lib().aln_autotune(self.dix._h, ctypes.byref(b), d["n"], ctypes.byref(p), ctypes.byref(r),
+                                 _stream_ptr(stream), ctypes.byref(ms)), "aln_autotune")
+        return dataclasses.replace(params, blocks_per_sm=p.blocks_per_sm), ms.value
+
+    def capture(self, d, params: Params, res, hits):
+        """Capture one search of the uploaded batch d into a CUDA graph; replay it
+        with graph.replay() for every new batch copied into the same buffers.
+        One replay at a time (the graph's queue counter is fixed)."""
+        t = self.torch
+        side = t.cuda.Stream(device=self.dev)
+        side.wait_stream(t.cuda.current_stream(self.dev))
+        with t.cuda.stream(side):  # warm-up outside the capture
+            self.search_device(d, params, res, hits, side)
+        t.cuda.current_stream(self.dev).wait_stream(side)
+        t.cuda.synchronize(self.dev)
+        g = t.cuda.CUDAGraph()
+        with t.cuda.graph(g):
+            self.search_device(d, params, res, hits, t.cuda.current_stream(self.dev))
+        return g
+
     def align(self, codes, offsets, lens, params: Params, z=None, stream=None):
         """Host arrays in, numpy (res[n], hits[n, hit_cap]) out."""
         d = self.upload(codes, offsets, lens, z)

@@ -102,6 +102,8 @@ SIGNATURES = {
     "aln_search": (ctypes.c_int, [P, ctypes.POINTER(aln_batch), ctypes.c_uint32,
                                   ctypes.POINTER(aln_params), ctypes.POINTER(aln_result), P]),
     "sa_to_pos": (ctypes.c_int, [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
+    "aln_autotune": (ctypes.c_int, [P, ctypes.POINTER(aln_batch), ctypes.c_uint32, ctypes.POINTER(aln_params),
+                                    ctypes.POINTER(aln_result), P, ctypes.POINTER(ctypes.c_float)]),
     "aln_search_noalloc": (ctypes.c_int, [P, ctypes.POINTER(aln_batch), ctypes.c_uint32,
                                           ctypes.POINTER(aln_params), ctypes.POINTER(aln_result), P]),
     "aln_pack_reads": (ctypes.c_int, [P, P, P, ctypes.c_uint32, P, P, P]),

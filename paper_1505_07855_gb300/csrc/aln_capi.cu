@@ -11,6 +11,7 @@
 #include "aln_search.cuh"
 
 namespace aln {
+int persistent_max_blocks(uint32_t z);
 cudaError_t launch_search(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
                           aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, cudaStream_t st);
 }
@@ -136,6 +137,48 @@ extern "C" int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t
                                   static_cast<cudaStream_t>(stream));
     if (prev != idx->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(e, "aln_search: launch");
+    return ALN_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+extern "C" int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint32_t n_reads, aln_params *params,
+                            aln_result *scratch, void *stream, float *best_ms) {
+    if (!idx || !sample || !params || !scratch || !n_reads)
+        return fail(ALN_EINVAL, "aln_autotune: null argument or empty sample");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != idx->device) cudaSetDevice(idx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int maxb = persistent_max_blocks(params->z);
+    aln_params p = *params;
+    p.mode = ALN_MODE_PERSISTENT;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = ALN_OK, best_b = 0;
+    float best = 0;
+    p.blocks_per_sm = static_cast<uint8_t>(maxb > 0 ? maxb : 1);
+    rc = aln_search(idx, sample, n_reads, &p, scratch, stream);  // warm-up
+    for (int b = 1; b <= maxb && rc == ALN_OK; b++) {
+        p.blocks_per_sm = static_cast<uint8_t>(b);
+        cudaEventRecord(e0, st);
+        rc = aln_search(idx, sample, n_reads, &p, scratch, stream);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ALN_EDEVICE, "aln_autotune: search failed");
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == ALN_OK && (best_b == 0 || ms < best)) {
+            best = ms;
+            best_b = b;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (prev != idx->device) cudaSetDevice(prev);
+    if (rc != ALN_OK) return rc;
+    params->blocks_per_sm = static_cast<uint8_t>(best_b);
+    if (best_ms) *best_ms = best;
     return ALN_OK;
 }
 

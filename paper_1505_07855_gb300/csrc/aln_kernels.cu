@@ -157,6 +157,17 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
     return cudaGetLastError();
 }
 
+// Resident blocks per SM of the persistent kernel for limit z (occupancy).
+int persistent_max_blocks(uint32_t z) {
+    int per_sm = 0;
+    switch (stack_cap_for(z)) {
+        case 19: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<19>, kThreads, 0); break;
+        case 37: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<37>, kThreads, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<64>, kThreads, 0); break;
+    }
+    return per_sm;
+}
+
 cudaError_t launch_search(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
                           aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, cudaStream_t st) {
     if (n == 0) return cudaSuccess;

@@ -213,3 +213,31 @@ def test_chr100_full_size_sampled(cuda):
     sub = w.reads.subset(sample)
     ro, ho, _ = oracle_align(pair.ox, sub, w.params, 32, oracle.BEST1)
     compare(rp[sample], hp[sample], ro, ho, idx=sample, what="chr100 full")
+
+
+def test_autotune_and_graph_replay(cuda, tiny36):
+    """The autotuner picks a feasible blocks-per-SM value whose results equal the
+    default's; a search captured in a CUDA graph and replayed twice (with the
+    input buffers refilled in between) gives the direct results."""
+    w, pair = tiny36
+    al = pair.al
+    torch = cuda
+    p = aln.Params.from_limits(w.params, hit_cap=16, mode=aln.MODE_PERSISTENT)
+    d = al.upload(w.reads.codes, w.reads.offsets, w.reads.lens)
+    res, hits = al.outputs(d["n"], 16)
+    tuned, ms = al.autotune(d, p, res, hits)
+    assert 1 <= tuned.blocks_per_sm <= 16 and ms > 0
+    ref = al.align(w.reads.codes, w.reads.offsets, w.reads.lens, p)
+    got = al.align(w.reads.codes, w.reads.offsets, w.reads.lens, tuned)
+    assert np.array_equal(ref[0], got[0])
+    g = al.capture(d, p, res, hits)
+    for _ in range(2):
+        res.fill_(0)
+        hits.fill_(0)
+        d2 = al.upload(w.reads.codes, w.reads.offsets, w.reads.lens)
+        for key in ("bases", "nmask", "offsets", "lens"):
+            d[key].copy_(d2[key])
+        g.replay()
+        torch.cuda.synchronize()
+        r = res.cpu().numpy().view(aln.RES_DTYPE)[:d["n"]]
+        assert np.array_equal(r, ref[0])
