@@ -331,8 +331,12 @@ def run_gpu(args):
             aln.Index.build(w.text, kmer_k=args.kmer_k).save(path)
         torch.distributed.barrier()
         hix = aln.Index.load(path)
+    elif args.index_cache and os.path.exists(args.index_cache):
+        hix = aln.Index.load(args.index_cache)
     else:
         hix = aln.Index.build(w.text, kmer_k=args.kmer_k)
+        if args.index_cache:
+            hix.save(args.index_cache)
     t_build = time.time() - t0
     dix = hix.to_device(local)
     al = aln.Aligner(dix)
@@ -581,6 +585,7 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--work-limit", type=int, default=0, help="node expansions per read (0 = library default)")
     ap.add_argument("--autotune", action="store_true", help="choose blocks per SM with aln_autotune first")
+    ap.add_argument("--index-cache", default="", help="load the index image from this file, or build and save it")
     ap.add_argument("--graph", action="store_true", help="time the persistent form as CUDA-graph replays")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=2000)
