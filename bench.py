@@ -118,6 +118,29 @@ def _dist():
     return ws, rank, local
 
 
+def replica_index(aln, text, kmer_k, rank, ws, barrier, path):
+    """Replicas: rank 0 builds the index and saves it, the other ranks load the
+    image after the barrier (no collective touches the data path)."""
+    if ws > 1:
+        if rank == 0:
+            aln.Index.build(text, kmer_k=kmer_k).save(path)
+        barrier()
+        return aln.Index.load(path)
+    return aln.Index.build(text, kmer_k=kmer_k)
+
+
+def max_over_ranks(values, ws, device=None):
+    """Element-wise maximum of per-rank timings (the whole job is as slow as its
+    slowest replica)."""
+    if ws <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 def oracle_sample(w, n_sample, threads, seed=7):
     """Oracle index of the text and its results on a seeded sample of reads."""
     import oracle
@@ -326,11 +349,8 @@ def run_gpu(args):
     # index: rank 0 builds and saves, the other replicas load the image
     t0 = time.time()
     if ws > 1:
-        path = f"/tmp/aln_bench_{args.workload}.fmi"
-        if rank == 0:
-            aln.Index.build(w.text, kmer_k=args.kmer_k).save(path)
-        torch.distributed.barrier()
-        hix = aln.Index.load(path)
+        hix = replica_index(aln, w.text, args.kmer_k, rank, ws, torch.distributed.barrier,
+                            f"/tmp/aln_bench_{args.workload}.fmi")
     elif args.index_cache and os.path.exists(args.index_cache):
         hix = aln.Index.load(args.index_cache)
     else:
@@ -404,10 +424,7 @@ def run_gpu(args):
     clocks = clk.summary()
     ms_head = float(np.mean(times["persistent"]))
     ms_plain = float(np.mean(times["plain"]))
-    if ws > 1:
-        t = torch.tensor([ms_head, ms_plain], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_head, ms_plain = float(t[0]), float(t[1])
+    ms_head, ms_plain = max_over_ranks([ms_head, ms_plain], ws, dev)
     rp, hp = out["plain"]
     rq, hq = out["persistent"]
     inc = ((rp["flags"] | rq["flags"]) & aln.FLAG_INCOMPLETE) != 0
