@@ -57,7 +57,7 @@ extern "C" {
 #define ALN_MAX_Z 7          /* largest difference limit; larger per-read z is flagged */
 #define ALN_MAX_HIT_CAP 255
 #define ALN_MAX_KMER_K 12
-#define ALN_CAND_CAP 64      /* distinct candidate hits kept per read by the kernels */
+#define ALN_CAND_CAP 512     /* distinct candidate hits kept per read by the kernels */
 
 /* ---------------------------------------------------------------- per-read flags */
 #define ALN_FLAG_HIT_OVERFLOW 0x01   /* more kept hits than hit_cap: list truncated,

@@ -18,7 +18,7 @@ ALN_EAGAIN = -7
 MAX_READ_LEN = 255
 MAX_Z = 7
 MAX_HIT_CAP = 255
-CAND_CAP = 64
+CAND_CAP = 512
 FLAG_HIT_OVERFLOW = 0x01
 FLAG_STACK_OVERFLOW = 0x02
 FLAG_CAND_OVERFLOW = 0x04
