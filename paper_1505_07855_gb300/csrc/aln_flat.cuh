@@ -207,39 +207,41 @@ struct FlatLane {
         has_next = true;
     }
 
-    // Children of the node in cur / cbits given its four extensions.
+    // Children of the node in cur / cbits given its four extensions.  Push order:
+    // the match child, mismatches by base, the insertion, deletions by base (the
+    // match child lowest, so that the alternatives are expanded first).  Only the
+    // children that exist are visited, through a bit mask in that order.
     __device__ __forceinline__ void push_children(const uint32_t lo4[4], const uint32_t hi4[4]) {
         const uint32_t info = cur.z;
         const uint32_t i = info & 0xFFu, mm = (info >> 8) & 7u, go = (info >> 11) & 7u, ge = (info >> 14) & 7u;
         const uint32_t ni = (info >> 17) & 7u, sd = (info >> 20) & 7u, last = (info >> 23) & 3u;
-        const bool allowM = cbits & 1u, mm_ok = cbits & 2u, ins_ok = cbits & 4u, del_ok = cbits & 8u;
         const uint32_t qi = (cbits >> 4) & 3u;
         const bool isN = cbits & 64u;
         const uint32_t sd2 = sd + ((cbits >> 7) & 1u);
-        const bool grow = cbits & 256u;  // the node's target is shorter than k: track child ids
-        const uint32_t cid = grow ? cur.w << 2 : 0u;
-        const uint32_t mlo = qi == 0 ? lo4[0] : (qi == 1 ? lo4[1] : (qi == 2 ? lo4[2] : lo4[3]));
-        const uint32_t mhi = qi == 0 ? hi4[0] : (qi == 1 ? hi4[1] : (qi == 2 ? hi4[2] : hi4[3]));
-        if (allowM && mhi > mlo) push(mlo, mhi, pack_info(i + 1, mm, go, ge, ni, sd, OP_M), cid | qi);
-        if (mm_ok) {
+        const uint32_t cid = (cbits & 256u) ? cur.w << 2 : 0u;  // track child ids below depth k
+        uint32_t ne = 0;
 #pragma unroll
-            for (uint32_t c = 0; c < 4; c++)
-                if ((c != qi || isN) && hi4[c] > lo4[c])
-                    push(lo4[c], hi4[c], pack_info(i + 1, mm + 1, go, ge, ni, sd2, OP_M), cid | c);
-        }
-        if (ins_ok)
-            push(cur.x, cur.y,
-                 last == OP_I ? pack_info(i + 1, mm, go, ge + 1, ni + 1, sd2, OP_I)
-                              : pack_info(i + 1, mm, go + 1, ge, ni + 1, sd2, OP_I),
-                 cur.w);
-        if (del_ok) {
-#pragma unroll
-            for (uint32_t c = 0; c < 4; c++)
-                if (hi4[c] > lo4[c])
-                    push(lo4[c], hi4[c],
-                         last == OP_D ? pack_info(i, mm, go, ge + 1, ni, sd2, OP_D)
-                                      : pack_info(i, mm, go + 1, ge, ni, sd2, OP_D),
-                         cid | c);
+        for (uint32_t c = 0; c < 4; c++) ne |= (hi4[c] > lo4[c] ? 1u : 0u) << c;
+        uint32_t mask = 0;
+        if ((cbits & 1u) && ((ne >> qi) & 1u)) mask |= 1u;
+        if (cbits & 2u) mask |= (ne & (isN ? 0xFu : (0xFu & ~(1u << qi)))) << 1;
+        if (cbits & 4u) mask |= 1u << 5;
+        if (cbits & 8u) mask |= ne << 6;
+        const uint32_t infoM = pack_info(i + 1, mm, go, ge, ni, sd, OP_M);
+        const uint32_t infoX = pack_info(i + 1, mm + 1, go, ge, ni, sd2, OP_M);
+        const uint32_t infoI = last == OP_I ? pack_info(i + 1, mm, go, ge + 1, ni + 1, sd2, OP_I)
+                                            : pack_info(i + 1, mm, go + 1, ge, ni + 1, sd2, OP_I);
+        const uint32_t infoD = last == OP_D ? pack_info(i, mm, go, ge + 1, ni, sd2, OP_D)
+                                            : pack_info(i, mm, go + 1, ge, ni, sd2, OP_D);
+        while (mask) {
+            const uint32_t b = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const bool kM = b == 0, kX = b >= 1 && b <= 4, kI = b == 5;
+            const uint32_t c = kM ? qi : (kX ? b - 1 : (b >= 6 ? b - 6 : 0u));
+            const uint32_t clo = c == 0 ? lo4[0] : (c == 1 ? lo4[1] : (c == 2 ? lo4[2] : lo4[3]));
+            const uint32_t chi = c == 0 ? hi4[0] : (c == 1 ? hi4[1] : (c == 2 ? hi4[2] : hi4[3]));
+            push(kI ? cur.x : clo, kI ? cur.y : chi, kM ? infoM : (kX ? infoX : (kI ? infoI : infoD)),
+                 kI ? cur.w : (cid | c));
         }
     }
 

@@ -27,6 +27,8 @@ namespace aln {
 //  3 table fetches            4 warp-level fetch issues    5 lanes at those issues
 //  6 reads finished           7 control rounds             8 stack pops
 //  9 warp trips                10 live lanes at those trips
+// 11 cycles in control         12 cycles in fetch + apply   13 cycles in the hand-over
+//    (11-13 measured by lane 0 of each warp between warp re-formations)
 __device__ unsigned long long g_stats[16];
 #define STAT_ADD(i, v) atomicAdd(&g_stats[i], static_cast<unsigned long long>(v))
 #endif
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
     L.rv = L.own_rv;
 #ifdef ALN_STATS
     unsigned long long st_it = 0, st_f = 0, st_occ = 0, st_tab = 0, st_wi = 0, st_wl = 0, st_wa = 0, st_wal = 0;
+    unsigned long long st_cc = 0, st_cf = 0, st_ce = 0;
 #endif
     // All 32 lanes of the warp stay in the loop until every lane is free and the
     // queue is empty; each trip is: control, one converged fetch, the hand-over.
@@ -84,8 +87,14 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
     // most work_limit expansions; the guard only caps a bug.
     for (unsigned long long it = 0; it < (1ull << 44); it++) {
         FetchReq fr;
+#ifdef ALN_STATS
+        const unsigned long long k0 = clock64();
+#endif
         L.control(X, rb, n_reads, p, res, hits, queue, sb, sn, fr);
         __syncwarp();
+#ifdef ALN_STATS
+        const unsigned long long k1 = clock64();
+#endif
 #ifdef ALN_STATS
         st_it++;
         {
@@ -111,13 +120,25 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
             fetch4(X, fr, lo4, hi4);
             L.apply(X, lo4, hi4);
         }
+#ifdef ALN_STATS
+        __syncwarp();
+        const unsigned long long k2 = clock64();
+#endif
         L.exchange(lane, s_bases, s_nmask, warp_col);
+#ifdef ALN_STATS
+        if (lane == 0) {
+            st_cc += k1 - k0;
+            st_cf += k2 - k1;
+            st_ce += clock64() - k2;
+        }
+#endif
         if (__ballot_sync(0xFFFFFFFFu, L.phase != PH_FREE) == 0) break;
     }
 #ifdef ALN_STATS
     STAT_ADD(0, st_it); STAT_ADD(1, st_f); STAT_ADD(2, st_occ); STAT_ADD(3, st_tab);
     STAT_ADD(4, st_wi); STAT_ADD(5, st_wl); STAT_ADD(6, L.st_reads); STAT_ADD(7, L.st_rounds);
     STAT_ADD(8, L.st_pops); STAT_ADD(9, st_wa); STAT_ADD(10, st_wal);
+    STAT_ADD(11, st_cc); STAT_ADD(12, st_cf); STAT_ADD(13, st_ce);
 #endif
 }
 
