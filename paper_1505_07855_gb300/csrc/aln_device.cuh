@@ -64,6 +64,55 @@ __device__ __forceinline__ uint32_t sym_mask(int k) {
     return __funnelshift_lc(0xFFFFFFFFu, 0u, 2u * static_cast<uint32_t>(k)) & 0x55555555u;
 }
 
+// The half of a block a row at offset o counts over: the 4 counts and the 6
+// symbol words of its half (words 0..5 backwards from the middle, 6..11
+// forwards), read as 3 of the block's 4 quads.
+struct HalfBlock {
+    uint32_t cnt[4];
+    uint32_t w[6];
+};
+
+__device__ __forceinline__ void load_half(const uint4 *blocks, uint32_t b, uint32_t o, HalfBlock &H) {
+    const uint4 *p = blocks + 4ull * b;
+    const bool up = o >= kHalfRows;
+    const uint4 q0 = ld_nc(p), q2 = ld_nc(p + 2), qx = ld_nc(p + (up ? 3 : 1));
+    H.cnt[0] = q0.x; H.cnt[1] = q0.y; H.cnt[2] = q0.z; H.cnt[3] = q0.w;
+    if (up) {
+        H.w[0] = q2.z; H.w[1] = q2.w; H.w[2] = qx.x; H.w[3] = qx.y; H.w[4] = qx.z; H.w[5] = qx.w;
+    } else {
+        H.w[0] = qx.x; H.w[1] = qx.y; H.w[2] = qx.z; H.w[3] = qx.w; H.w[4] = q2.x; H.w[5] = q2.y;
+    }
+}
+
+// occ_before(c, 192 b + o) from the row's half block (before the $ correction).
+__device__ __forceinline__ void occ4_in_half(const HalfBlock &H, uint32_t o, uint32_t occ[4]) {
+    const bool up = o >= kHalfRows;
+    const int x = static_cast<int>(up ? o - kHalfRows : o);
+    uint32_t nlo = 0, nhi = 0, nboth = 0;
+#pragma unroll
+    for (int pr = 0; pr < 3; pr++) {
+        const uint32_t wa = H.w[2 * pr], wb = H.w[2 * pr + 1];
+        uint32_t ma = sym_mask(x - 32 * pr), mb = sym_mask(x - 32 * pr - 16);
+        if (!up) {
+            ma ^= 0x55555555u;
+            mb ^= 0x55555555u;
+        }
+        const uint32_t la = wa & ma, ha = (wa >> 1) & ma;
+        const uint32_t lb = wb & mb, hb = (wb >> 1) & mb;
+        nlo += __popc(la | (lb << 1));
+        nhi += __popc(ha | (hb << 1));
+        nboth += __popc((la & ha) | ((lb & hb) << 1));
+    }
+    const uint32_t nsym = up ? static_cast<uint32_t>(x) : kHalfRows - static_cast<uint32_t>(x);
+    const uint32_t cT = nboth, cG = nhi - nboth, cC = nlo - nboth;
+    const uint32_t cA = nsym - cT - cG - cC;
+    if (up) {
+        occ[0] = H.cnt[0] + cA; occ[1] = H.cnt[1] + cC; occ[2] = H.cnt[2] + cG; occ[3] = H.cnt[3] + cT;
+    } else {
+        occ[0] = H.cnt[0] - cA; occ[1] = H.cnt[1] - cC; occ[2] = H.cnt[2] - cG; occ[3] = H.cnt[3] - cT;
+    }
+}
+
 // occ_before(c, 192 b + o) for all four bases (before the $ correction).
 __device__ __forceinline__ void occ4_in_block(const Block &B, uint32_t o, uint32_t occ[4]) {
     const bool up = o >= kHalfRows;
@@ -106,13 +155,13 @@ __device__ __forceinline__ void lf4(const DText &T, uint32_t lo, uint32_t hi, ui
         return;
     }
     const uint32_t blo = lo / kRowsPerBlock, bhi = hi / kRowsPerBlock;
-    Block Bl, Bh;
-    load_block(T.blocks, blo, Bl);
-    if (bhi != blo) load_block(T.blocks, bhi, Bh);
-    else Bh = Bl;
+    const uint32_t ol = lo - blo * kRowsPerBlock, oh = hi - bhi * kRowsPerBlock;
+    HalfBlock Hl, Hh;
+    load_half(T.blocks, blo, ol, Hl);  // both reads issued before either is used
+    load_half(T.blocks, bhi, oh, Hh);
     uint32_t olo[4], ohi[4];
-    occ4_in_block(Bl, lo - blo * kRowsPerBlock, olo);
-    occ4_in_block(Bh, hi - bhi * kRowsPerBlock, ohi);
+    occ4_in_half(Hl, ol, olo);
+    occ4_in_half(Hh, oh, ohi);
     olo[0] -= (lo > T.primary) ? 1u : 0u;
     ohi[0] -= (hi > T.primary) ? 1u : 0u;
 #pragma unroll
