@@ -32,17 +32,17 @@ BYTES_PER_LOOKUP = 64
 # DRAM bytes (read + write) of aln_persistent_kernel from one ncu capture of the
 # chr100 workload (300 000 reads, scaled per read; profiles/aln_persistent_chr100.md).
 # Used only while the kernel sources hash to the value they had at capture time.
-TRAFFIC_CAPTURE = {"src_sha256_16": "8772304fd6dc5c17", "workload": "chr100", "dram_bytes_per_read": 23960.0}
+KERNEL_SOURCES = ("aln_device.cuh", "aln_search.cuh", "aln_flat.cuh", "aln_kernels.cu")
+TRAFFIC_CAPTURE = {"src_sha256_16": "7834fc4f3d38a9fb", "workload": "chr100", "dram_bytes_per_read": 23960.0}
 
 
 def _src_hash() -> str:
-    import glob
+    """Hash of the sources the search kernel is compiled from."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1505_07855_gb300", "csrc", "*")))
-    for f in files + [os.path.join(ROOT, "include", "aln_gb300.h")]:
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for f in KERNEL_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(ROOT, "paper_1505_07855_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -284,6 +284,65 @@ def property_checks(w, outp, pos, npos, hit_cap, n_hits, valid, n_sample=400, se
             "origin_recall": found / max(1, eligible)}
 
 
+def gather_probe_phase(aln, torch, dev, stream, buf_gib=4, n_gathers=1 << 27, best_of=10, warmup=3):
+    """Random 64-byte block-read rate over a buffer far larger than L2 (best of
+    best_of launches, CUDA events on the launching stream)."""
+    buf = torch.empty(buf_gib << 30, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    ms = []
+    with torch.cuda.stream(stream):
+        buf.fill_(0x5A)
+        for it in range(warmup + best_of):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            aln.gather_probe(buf, n_gathers, it, sink, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= warmup:
+                ms.append(e0.elapsed_time(e1))
+    del buf
+    best = min(ms)
+    return {"gbs": n_gathers * 64 / (best / 1000) / 1e9, "unit": "GB/s", "buffer_bytes": buf_gib << 30,
+            "gathers_per_launch": n_gathers, "bytes_per_gather": 64, "best_of": best_of, "ms": best}
+
+
+def accuracy_report(w, outp, pos, npos, hit_cap, valid):
+    """Placement against the simulated origin: a read counts as placed correctly
+    when a hit of its best stratum (n_diff == d_best) on the read's true strand
+    has a position within z bases of the true start.  Hits wider than 16 rows
+    have no positions; reads whose best stratum is all such hits are
+    'unresolved' (repeats)."""
+    rg, hg = outp
+    n = rg.size
+    rows = np.nonzero(valid)[0]
+    hv = hg[valid]
+    nh = hv.size
+    widths = npos.cpu().numpy().view(np.uint32)[:nh].astype(np.int64)
+    p = pos.cpu().numpy().view(np.uint64)[:nh * 16].reshape(-1, 16).astype(np.int64) if nh else np.zeros((0, 16), np.int64)
+    tp = w.reads.true_pos.astype(np.int64)
+    ts = w.reads.true_strand.astype(np.int64)
+    z = w.reads.z.astype(np.int64) if np.any(w.reads.z) else np.full(n, int(w.params["z"]), np.int64)
+    best = hv["n_diff"].astype(np.int64) == rg["d_best"][rows].astype(np.int64)
+    resolved = widths <= 16
+    near = (np.arange(16)[None, :] < np.where(resolved, widths, 0)[:, None]) & \
+           (np.abs(p - tp[rows][:, None]) <= z[rows][:, None])
+    hit_ok = best & (hv["strand"].astype(np.int64) == ts[rows]) & near.any(axis=1)
+    ok = np.bincount(rows, weights=hit_ok, minlength=n) > 0
+    best_resolved = np.bincount(rows, weights=best & resolved, minlength=n) > 0
+    mapped = rg["n_hits"] > 0
+    unique = mapped & (rg["c0"] == 1)
+    out = {"reads": int(n), "mapped": float(mapped.mean()), "best_covers_origin": float(ok.mean()),
+           "unresolved_repeats": float((mapped & ~best_resolved).mean()),
+           "unique_best": float(unique.mean()),
+           "unique_best_correct": float(ok[unique].mean()) if unique.any() else None,
+           "tolerance": "z bases"}
+    lens = w.reads.lens.astype(np.int64)
+    if np.unique(lens).size > 1:
+        out["best_covers_origin_by_len"] = {int(m): float(ok[lens == m].mean()) for m in np.unique(lens)}
+    return out
+
+
 def run_reference(args):
     """CPU oracle arm: each step aligns a bounded seeded sample on all host cores."""
     ws, rank, _ = _dist()
@@ -508,6 +567,13 @@ def run_gpu(args):
                                 indel_end_skip=lim["indel_end_skip"], hit_cap=hit_cap, threads=threads)
         t_align = time.time() - t0
         cpu_v = sel.size / t_align
+        sel1 = sel[: min(1000, sel.size)]
+        sub1 = w.reads.subset(sel1)
+        t0 = time.time()
+        ox.align(sub1.codes, sub1.offsets, sub1.lens, sub1.z, z_default=lim["z"], max_gapo=lim["max_gapo"],
+                 max_gape=lim["max_gape"], seed_len=lim["seed_len"], seed_z=lim["seed_z"],
+                 indel_end_skip=lim["indel_end_skip"], hit_cap=hit_cap, threads=1)
+        cpu_v1 = sel1.size / (time.time() - t0)
         # parity of the timed outputs on the sample
         rg, hg = out["persistent"]
         rg, hg = rg[sel], hg[sel]
@@ -527,6 +593,7 @@ def run_gpu(args):
                             "bytes_per_read": lookups_per_read * BYTES_PER_LOOKUP,
                             "occ_lookups_per_s": lookups_per_read * n / (ms_head / 1000)}
         line["cpu_baseline"] = {"value": cpu_v, "unit": "reads/s", "cores": threads, "kind": "oracle",
+                                "value_1thread": cpu_v1,
                                 "sample": f"{sel.size} seeded reads of the {n}-read batch, "
                                           f"oracle index build ({t_index:.1f} s) not timed"}
         line["parity"] = {"sampled_reads": int(sel.size), "bit_exact": bool(ok)}
@@ -553,6 +620,12 @@ def run_gpu(args):
     n_pos = int(np_h[np_h <= 16].sum())
     line["sa_to_pos"] = {"hits": int(hits_all.size), "positions": n_pos, "ms": float(np.mean(sa_ms)),
                          "positions_per_s": n_pos / (np.mean(sa_ms) / 1000)}
+    if rank == 0:
+        line["accuracy"] = accuracy_report(w, out["persistent"], pos, npos, hit_cap, valid)
+    if args.gather_probe:
+        line["gather_probe"] = gather_probe_phase(aln, torch, dev, stream)
+        if "roofline" in line:
+            line["roofline"]["frac_of_gather_probe"] = line["roofline"]["achieved"] / line["gather_probe"]["gbs"]
     if not use_oracle and rank == 0 and not args.no_oracle:
         line["parity"] = property_checks(w, out["persistent"], pos, npos, hit_cap, hits_all.size, valid)
     if use_oracle:
@@ -606,6 +679,8 @@ def main():
     ap.add_argument("--graph", action="store_true", help="time the persistent form as CUDA-graph replays")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=2000)
+    ap.add_argument("--gather-probe", type=int, default=1,
+                    help="1: measure the random 64-byte gather rate over a 4 GiB buffer (aln_gather_probe)")
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--reads", type=int, default=0, help="use only the first N reads (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)

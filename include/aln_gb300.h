@@ -306,6 +306,27 @@ void aln_server_destroy(aln_server *s);
 int aln_search_noalloc(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
                        const aln_params *params, aln_result *out, void *stream);
 
+/* ---------------------------------------------------------------- measurement
+ *
+ * Random 64-byte gather rate of the device memory, the bound of the LF step's
+ * access pattern (Sec. 2: each processed base reads index data at a position
+ * that depends on the previous one; over a large index these are scattered
+ * 64-byte blocks).  aln_gather_probe reads n_gathers 64-byte blocks of buf:
+ * gather g (0 <= g < n_gathers) reads block
+ *     b(g) = (h(g + seed * 0x9E3779B9) * n_blocks) >> 32    (32-bit wrap-around),
+ * n_blocks = buf_bytes / 64, h = the "lowbias32" integer hash (x ^= x >> 16;
+ * x *= 0x7feb352d; x ^= x >> 15; x *= 0x846ca68b; x ^= x >> 16).  Four threads
+ * read the four 16-byte quarters of one block; every thread keeps 8 gathers in
+ * flight; the grid fills every SM.  *sink (device memory, 4 bytes) is XORed
+ * (atomically) with the XOR of all 16 words of every gathered block, so the
+ * loads cannot be dropped and the result is checkable.  buf is device memory,
+ * 64-byte aligned, 64 <= buf_bytes < 2^38 (n_blocks < 2^32); n_gathers < 2^32.
+ * Launches on the device that holds buf, asynchronous on stream (time it with
+ * events on that stream).  Errors: ALN_EINVAL (null, misaligned, size out of
+ * range, not device memory), ALN_EDEVICE (launch). */
+int aln_gather_probe(const void *buf, uint64_t buf_bytes, uint64_t n_gathers, uint32_t seed,
+                     uint32_t *sink, void *stream);
+
 /* Host helper: pack reads (codes 0..4, read r at codes[code_offset[r]] of
  * length len[r]) back to back into the aln_batch layout.  bases_out needs
  * ceil(total/16) words, nmask_out ceil(total/32) words (total = sum of len),

@@ -27,7 +27,7 @@ from ._lib import (  # noqa: F401
     RES_DTYPE, STRATA_BEST1, STRATA_FULL, check, lib, library_path,
 )
 
-__all__ = ["Index", "DeviceIndex", "Params", "Aligner", "pack_reads", "HIT_DTYPE", "RES_DTYPE"]
+__all__ = ["Index", "DeviceIndex", "Params", "Aligner", "pack_reads", "gather_probe", "HIT_DTYPE", "RES_DTYPE"]
 
 
 def _ptr(a) -> int | None:
@@ -126,6 +126,14 @@ class DeviceIndex:
         if h is not None and h.value:
             lib().fm_dindex_free(h)
             self._h = None
+
+
+def gather_probe(buf, n_gathers: int, seed: int, sink, stream=None) -> None:
+    """aln_gather_probe: n_gathers random 64-byte block reads of the device tensor
+    buf; sink (a device int32/uint32 tensor of one element) is XORed with the XOR
+    of every gathered block's 16 words."""
+    check(lib().aln_gather_probe(_ptr(buf), buf.numel() * buf.element_size(), n_gathers, seed, _ptr(sink),
+                                 _stream_ptr(stream)), "aln_gather_probe")
 
 
 @dataclasses.dataclass

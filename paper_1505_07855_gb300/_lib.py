@@ -106,6 +106,7 @@ SIGNATURES = {
                                     ctypes.POINTER(aln_result), P, ctypes.POINTER(ctypes.c_float)]),
     "aln_search_noalloc": (ctypes.c_int, [P, ctypes.POINTER(aln_batch), ctypes.c_uint32,
                                           ctypes.POINTER(aln_params), ctypes.POINTER(aln_result), P]),
+    "aln_gather_probe": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, P, P]),
     "aln_pack_reads": (ctypes.c_int, [P, P, P, ctypes.c_uint32, P, P, P]),
     "aln_server_create": (ctypes.c_int, [P, ctypes.POINTER(aln_server_config), ctypes.POINTER(P)]),
     "aln_server_submit": (ctypes.c_int, [P, P, P, P, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]),

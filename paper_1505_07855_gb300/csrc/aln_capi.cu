@@ -342,6 +342,97 @@ extern "C" int aln_search_noalloc(const fm_dindex *idx, const aln_batch *batch, 
     return rc;
 }
 
+// ---------------------------------------------------------------- aln_gather_probe
+//
+// Random 64-byte block reads over a caller buffer: the denominator for the
+// LF step's scattered block reads.  Four lanes read the four 16-byte quarters
+// of one block, so one warp load instruction covers 8 blocks; each lane keeps
+// kProbeInFlight loads outstanding before it consumes any.
+
+namespace {
+constexpr int kProbeThreads = 256;
+constexpr int kProbeInFlight = 8;
+constexpr uint32_t kProbeGathersPerWarpRound = 8u * kProbeInFlight;
+
+// "lowbias32", a published 32-bit integer hash (two xorshift-multiply rounds).
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+__global__ void __launch_bounds__(kProbeThreads) gather_probe_kernel(const uint4 *__restrict__ buf, uint32_t n_blocks,
+                                                                     uint32_t n_gathers, uint32_t seed,
+                                                                     uint32_t *sink) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * kProbeThreads + threadIdx.x) >> 5;
+    const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * kProbeThreads) >> 5;
+    const uint32_t salt = seed * 0x9E3779B9u;
+    uint32_t acc = 0;
+    for (uint64_t g0 = warp * kProbeGathersPerWarpRound; g0 < n_gathers; g0 += n_warps * kProbeGathersPerWarpRound) {
+        uint4 v[kProbeInFlight];
+#pragma unroll
+        for (int u = 0; u < kProbeInFlight; u++) {
+            const uint64_t g = g0 + 8u * u + (lane >> 2);
+            v[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (g < n_gathers) {
+                const uint32_t b = __umulhi(lowbias32(static_cast<uint32_t>(g) + salt), n_blocks);
+                v[u] = ld_nc(buf + 4ull * b + (lane & 3u));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kProbeInFlight; u++) acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc ^= __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (lane == 0 && acc) atomicXor(sink, acc);
+}
+
+bool device_pointer(const void *p, int *device) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
+    *device = a.device;
+    return true;
+}
+}  // namespace
+
+extern "C" int aln_gather_probe(const void *buf, uint64_t buf_bytes, uint64_t n_gathers, uint32_t seed,
+                                uint32_t *sink, void *stream) {
+    if (!buf || !sink) return fail(ALN_EINVAL, "aln_gather_probe: null argument");
+    if (reinterpret_cast<uintptr_t>(buf) % 64) return fail(ALN_EINVAL, "aln_gather_probe: buf must be 64-byte aligned");
+    const uint64_t n_blocks = buf_bytes / 64;
+    if (n_blocks < 1 || n_blocks > 0xFFFFFFFFull)
+        return fail(ALN_EINVAL, "aln_gather_probe: buf_bytes must be in [64, 2^38)");
+    if (n_gathers > 0xFFFFFFFFull) return fail(ALN_EINVAL, "aln_gather_probe: n_gathers must be < 2^32");
+    int dev = 0, dev_sink = 0;
+    if (!device_pointer(buf, &dev) || !device_pointer(sink, &dev_sink) || dev != dev_sink)
+        return fail(ALN_EINVAL, "aln_gather_probe: buf and sink must be device memory of one device");
+    if (!n_gathers) return ALN_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gather_probe_kernel, kProbeThreads, 0);
+    const uint64_t per_block = static_cast<uint64_t>(kProbeThreads / 32) * kProbeGathersPerWarpRound;
+    const uint64_t need = (n_gathers + per_block - 1) / per_block;
+    const uint64_t full = static_cast<uint64_t>(sms > 0 ? sms : 1) * static_cast<uint64_t>(occ > 0 ? occ : 1);
+    const unsigned grid = static_cast<unsigned>(need < full ? need : full);
+    gather_probe_kernel<<<grid, kProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const uint4 *>(buf), static_cast<uint32_t>(n_blocks), static_cast<uint32_t>(n_gathers), seed, sink);
+    cudaError_t e = cudaGetLastError();
+    if (prev != dev) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "aln_gather_probe: launch");
+    return ALN_OK;
+}
+
 #ifdef ALN_STATS
 namespace aln {
 cudaError_t debug_stats(unsigned long long *out, int reset);
