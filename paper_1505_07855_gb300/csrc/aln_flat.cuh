@@ -233,6 +233,34 @@ struct FlatLane {
                                             : pack_info(i + 1, mm, go + 1, ge, ni + 1, sd2, OP_I);
         const uint32_t infoD = last == OP_D ? pack_info(i, mm, go, ge + 1, ni, sd2, OP_D)
                                             : pack_info(i, mm, go + 1, ge, ni, sd2, OP_D);
+        if (!mask) return;
+        // Fast form, no data-dependent loop: every existing child but the last
+        // goes to its stack slot (the displaced `next` first, then the children
+        // in mask order), the last becomes `next`.  This is exactly what pushing
+        // them one by one does whenever no push reaches the stack capacity.
+        const uint32_t nch = __popc(mask);
+        const int sp0 = sp + (has_next ? 1 : 0);
+        if (sp0 + static_cast<int>(nch) - 1 <= STACK_CAP) {
+            const uint32_t lastb = 31u - __clz(mask);
+            if (has_next) stk_set(sp, next);
+            const uint32_t loM = qi == 0 ? lo4[0] : (qi == 1 ? lo4[1] : (qi == 2 ? lo4[2] : lo4[3]));
+            const uint32_t hiM = qi == 0 ? hi4[0] : (qi == 1 ? hi4[1] : (qi == 2 ? hi4[2] : hi4[3]));
+#pragma unroll
+            for (uint32_t b = 0; b < 10; b++) {
+                const uint32_t c = b == 0 ? qi : (b <= 4 ? b - 1 : (b >= 6 ? b - 6 : 0u));
+                const uint4 e = b == 0   ? make_uint4(loM, hiM, infoM, cid | qi)
+                                : b <= 4 ? make_uint4(lo4[(b - 1) & 3u], hi4[(b - 1) & 3u], infoX, cid | c)
+                                : b == 5 ? make_uint4(cur.x, cur.y, infoI, cur.w)
+                                         : make_uint4(lo4[(b - 6) & 3u], hi4[(b - 6) & 3u], infoD, cid | c);
+                if (((mask >> b) & 1u) && b != lastb)
+                    stk_set(sp0 + static_cast<int>(__popc(mask & ((1u << b) - 1u))), e);
+                if (b == lastb) next = e;
+            }
+            sp = sp0 + static_cast<int>(nch) - 1;
+            has_next = true;
+            return;
+        }
+        // a push would reach the stack capacity: one by one (compaction, overflow flag)
         while (mask) {
             const uint32_t b = __ffs(mask) - 1;
             mask &= mask - 1;
