@@ -108,7 +108,7 @@ int fm_index_build(const uint8_t *text, uint64_t n, const fm_build_opts *opts, f
 void fm_index_free(fm_index *idx);
 int fm_index_info(const fm_index *idx, fm_index_info_t *info);
 
-/* Write / read the index image (little-endian binary, magic "ALNFMIX3").
+/* Write / read the index image (little-endian binary, magic "ALNFMIX4").
  * Load returns ALN_EIO on a missing, short or malformed file. */
 int fm_index_save(const fm_index *idx, const char *path);
 int fm_index_load(const char *path, fm_index **out);

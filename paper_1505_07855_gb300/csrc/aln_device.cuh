@@ -9,9 +9,10 @@
 //
 // Block layout (64 bytes per 192 rows): cnt[4] = occurrences of A, C, G, T
 // before the block's middle row (192 b + 96), $ and end padding counted as A;
-// then 12 words of 2-bit symbols (A=00 C=01 G=10 T=11), 16 per word.  A row at
-// offset o in the block counts forwards over symbols [96, o) or backwards over
-// [o, 96): at most 6 words, merged two words per popcount.
+// then 12 words of symbols (A=00 C=01 G=10 T=11), 6 for each half of the block:
+// the low-bit planes of symbols 0-31, 32-63, 64-95 of the half, then the
+// high-bit planes.  A row at offset o in the block counts forwards over symbols
+// [96, o) or backwards over [o, 96), inside one half: 3 masks, 9 popcounts.
 #pragma once
 
 #include <cstdint>
@@ -36,11 +37,6 @@ struct DIndex {
     uint32_t sa_shift;       // log2(sa_sample)
 };
 
-struct Block {
-    uint32_t cnt[4];
-    uint32_t w[12];
-};
-
 __device__ __forceinline__ uint4 ld_nc(const uint4 *p) {
     uint4 v;
     asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -49,24 +45,9 @@ __device__ __forceinline__ uint4 ld_nc(const uint4 *p) {
     return v;
 }
 
-__device__ __forceinline__ void load_block(const uint4 *blocks, uint32_t b, Block &B) {
-    const uint4 *p = blocks + 4ull * b;
-    uint4 q0 = ld_nc(p), q1 = ld_nc(p + 1), q2 = ld_nc(p + 2), q3 = ld_nc(p + 3);
-    B.cnt[0] = q0.x; B.cnt[1] = q0.y; B.cnt[2] = q0.z; B.cnt[3] = q0.w;
-    B.w[0] = q1.x; B.w[1] = q1.y; B.w[2] = q1.z; B.w[3] = q1.w;
-    B.w[4] = q2.x; B.w[5] = q2.y; B.w[6] = q2.z; B.w[7] = q2.w;
-    B.w[8] = q3.x; B.w[9] = q3.y; B.w[10] = q3.z; B.w[11] = q3.w;
-}
-
-// Mask of the low k symbols (k = 0..16) of a word, lo bit of each symbol only.
-__device__ __forceinline__ uint32_t sym_mask(int k) {
-    k = k < 0 ? 0 : (k > 16 ? 16 : k);
-    return __funnelshift_lc(0xFFFFFFFFu, 0u, 2u * static_cast<uint32_t>(k)) & 0x55555555u;
-}
-
 // The half of a block a row at offset o counts over: the 4 counts and the 6
-// symbol words of its half (words 0..5 backwards from the middle, 6..11
-// forwards), read as 3 of the block's 4 quads.
+// symbol words of its half (block words 4..9 below the middle, 10..15 above),
+// read as 3 of the block's 4 quads.
 struct HalfBlock {
     uint32_t cnt[4];
     uint32_t w[6];
@@ -84,24 +65,23 @@ __device__ __forceinline__ void load_half(const uint4 *blocks, uint32_t b, uint3
     }
 }
 
-// occ_before(c, 192 b + o) from the row's half block (before the $ correction).
+// Symbols of a half as bit planes: w[g] holds the low bits and w[3 + g] the
+// high bits of the half's symbols 32 g .. 32 g + 31 (bit j = symbol 32 g + j).
+// Counting symbols before (or from) position x of the half needs one mask per
+// 32 symbols, shared by both planes.
 __device__ __forceinline__ void occ4_in_half(const HalfBlock &H, uint32_t o, uint32_t occ[4]) {
     const bool up = o >= kHalfRows;
     const int x = static_cast<int>(up ? o - kHalfRows : o);
     uint32_t nlo = 0, nhi = 0, nboth = 0;
 #pragma unroll
-    for (int pr = 0; pr < 3; pr++) {
-        const uint32_t wa = H.w[2 * pr], wb = H.w[2 * pr + 1];
-        uint32_t ma = sym_mask(x - 32 * pr), mb = sym_mask(x - 32 * pr - 16);
-        if (!up) {
-            ma ^= 0x55555555u;
-            mb ^= 0x55555555u;
-        }
-        const uint32_t la = wa & ma, ha = (wa >> 1) & ma;
-        const uint32_t lb = wb & mb, hb = (wb >> 1) & mb;
-        nlo += __popc(la | (lb << 1));
-        nhi += __popc(ha | (hb << 1));
-        nboth += __popc((la & ha) | ((lb & hb) << 1));
+    for (int g = 0; g < 3; g++) {
+        const int k = max(x - 32 * g, 0);
+        uint32_t m = __funnelshift_lc(0xFFFFFFFFu, 0u, static_cast<uint32_t>(k));  // low min(k, 32) bits
+        if (!up) m = ~m;  // backwards: symbols at or after o
+        const uint32_t l = H.w[g] & m, h = H.w[3 + g] & m;
+        nlo += __popc(l);
+        nhi += __popc(h);
+        nboth += __popc(l & h);
     }
     const uint32_t nsym = up ? static_cast<uint32_t>(x) : kHalfRows - static_cast<uint32_t>(x);
     const uint32_t cT = nboth, cG = nhi - nboth, cC = nlo - nboth;
@@ -113,38 +93,18 @@ __device__ __forceinline__ void occ4_in_half(const HalfBlock &H, uint32_t o, uin
     }
 }
 
-// occ_before(c, 192 b + o) for all four bases (before the $ correction).
-__device__ __forceinline__ void occ4_in_block(const Block &B, uint32_t o, uint32_t occ[4]) {
-    const bool up = o >= kHalfRows;
-    const int x = static_cast<int>(up ? o - kHalfRows : o);
-    uint32_t nlo = 0, nhi = 0, nboth = 0;
-#pragma unroll
-    for (int pr = 0; pr < 3; pr++) {
-        const uint32_t wa = up ? B.w[6 + 2 * pr] : B.w[2 * pr];
-        const uint32_t wb = up ? B.w[7 + 2 * pr] : B.w[2 * pr + 1];
-        uint32_t ma = sym_mask(x - 32 * pr), mb = sym_mask(x - 32 * pr - 16);
-        if (!up) {  // backwards: symbols at or after o
-            ma ^= 0x55555555u;
-            mb ^= 0x55555555u;
-        }
-        const uint32_t la = wa & ma, ha = (wa >> 1) & ma;
-        const uint32_t lb = wb & mb, hb = (wb >> 1) & mb;
-        nlo += __popc(la | (lb << 1));
-        nhi += __popc(ha | (hb << 1));
-        nboth += __popc((la & ha) | ((lb & hb) << 1));
-    }
-    const uint32_t nsym = up ? static_cast<uint32_t>(x) : kHalfRows - static_cast<uint32_t>(x);
-    const uint32_t cT = nboth, cG = nhi - nboth, cC = nlo - nboth;
-    const uint32_t cA = nsym - cT - cG - cC;
-    if (up) {
-        occ[0] = B.cnt[0] + cA; occ[1] = B.cnt[1] + cC; occ[2] = B.cnt[2] + cG; occ[3] = B.cnt[3] + cT;
-    } else {
-        occ[0] = B.cnt[0] - cA; occ[1] = B.cnt[1] - cC; occ[2] = B.cnt[2] - cG; occ[3] = B.cnt[3] - cT;
-    }
+// The symbol at offset o of the block, from its half.
+__device__ __forceinline__ uint32_t sym_in_half(const HalfBlock &H, uint32_t o) {
+    const uint32_t x = o >= kHalfRows ? o - kHalfRows : o;
+    const uint32_t g = x >> 5, j = x & 31u;
+    const uint32_t l = g == 0 ? H.w[0] : (g == 1 ? H.w[1] : H.w[2]);
+    const uint32_t h = g == 0 ? H.w[3] : (g == 1 ? H.w[4] : H.w[5]);
+    return ((l >> j) & 1u) | (((h >> j) & 1u) << 1);
 }
 
-// Extend [lo, hi) by every base: children (lo4[c], hi4[c]).  Both block reads
-// are issued before either is used; a second read of the same block is skipped.
+// Extend [lo, hi) by every base: children (lo4[c], hi4[c]).  Both half-block
+// reads are issued before either is used (a second read of the same half is an
+// L1 hit).
 __device__ __forceinline__ void lf4(const DText &T, uint32_t lo, uint32_t hi, uint32_t lo4[4], uint32_t hi4[4]) {
     if (lo == 0 && hi == T.n + 1) {  // the empty string: children are the C ranges
 #pragma unroll
@@ -183,11 +143,11 @@ __device__ __forceinline__ void lf1(const DText &T, uint32_t c, uint32_t &lo, ui
 // suffix that starts one text position earlier.
 __device__ __forceinline__ uint32_t lf_row(const DText &T, uint32_t r) {
     const uint32_t b = r / kRowsPerBlock, o = r - b * kRowsPerBlock;
-    Block B;
-    load_block(T.blocks, b, B);
-    const uint32_t c = (B.w[o >> 4] >> (2 * (o & 15u))) & 3u;
+    HalfBlock H;
+    load_half(T.blocks, b, o, H);
+    const uint32_t c = sym_in_half(H, o);
     uint32_t occ[4];
-    occ4_in_block(B, o, occ);
+    occ4_in_half(H, o, occ);
     uint32_t v = occ[c];
     if (c == 0) v -= (r > T.primary) ? 1u : 0u;
     return T.C1[c] + v;

@@ -228,19 +228,28 @@ static void pack_text(HostText &T, const uint8_t *y, uint64_t n, const uint32_t 
     for (int c = 1; c < 4; c++) T.C[c] = T.C[c - 1] + cnt[c - 1];
     for (uint64_t r = 0; r < rows; r++)
         if (sa[r] == 0) T.primary = r;
+    std::vector<uint32_t> hcount(nb * 4, 0);  // per block: symbols of its first half
     parallel_chunks(threads, nb, [&](int, uint64_t b0, uint64_t b1) {
         for (uint64_t b = b0; b < b1; b++) {
             uint32_t *w = &T.blocks[b * kBlockWords + 4];
-            uint32_t c4[4] = {0, 0, 0, 0};
+            uint32_t c4[4] = {0, 0, 0, 0}, h4[4] = {0, 0, 0, 0};
             for (uint32_t t = 0; t < kBlockRows; t++) {
                 uint64_t r = b * kBlockRows + t;
                 if (r >= rows) break;
                 uint32_t s = sa[r];
                 uint32_t sym = s == 0 ? 0u : y[s - 1];  // $ stored as A
-                w[t / 16] |= sym << (2 * (t % 16));
+                // bit planes per half: words 0-2 low bits, 3-5 high bits of
+                // the half's symbols 0-31, 32-63, 64-95
+                const uint32_t half = t / (kBlockRows / 2), u = t % (kBlockRows / 2);
+                w[6 * half + u / 32] |= (sym & 1u) << (u % 32);
+                w[6 * half + 3 + u / 32] |= (sym >> 1) << (u % 32);
                 c4[sym]++;
+                if (t < kBlockRows / 2) h4[sym]++;
             }
-            for (int c = 0; c < 4; c++) bcount[b * 4 + c] = c4[c];
+            for (int c = 0; c < 4; c++) {
+                bcount[b * 4 + c] = c4[c];
+                hcount[b * 4 + c] = h4[c];
+            }
         }
     });
     // counts before the middle row: prefix over earlier blocks + the block's first
@@ -248,11 +257,11 @@ static void pack_text(HostText &T, const uint8_t *y, uint64_t n, const uint32_t 
     // backward count from the middle of the last block stays exact.
     uint32_t run[4] = {0, 0, 0, 0};
     for (uint64_t b = 0; b < nb; b++) {
-        uint32_t half[4] = {0, 0, 0, 0};
-        for (uint32_t t = 0; t < kBlockRows / 2; t++)
-            half[(T.blocks[b * kBlockWords + 4 + t / 16] >> (2 * (t % 16))) & 3u]++;
+        // padding rows of the first half (stored as A)
+        const uint64_t mid = b * kBlockRows + kBlockRows / 2;
+        const uint32_t pad = mid > rows ? static_cast<uint32_t>(std::min<uint64_t>(kBlockRows / 2, mid - rows)) : 0u;
         for (int c = 0; c < 4; c++) {
-            T.blocks[b * kBlockWords + c] = run[c] + half[c];
+            T.blocks[b * kBlockWords + c] = run[c] + hcount[b * 4 + c] + (c == 0 ? pad : 0u);
             run[c] += bcount[b * 4 + c];
         }
     }
@@ -361,7 +370,7 @@ extern "C" int fm_index_info(const fm_index *idx, fm_index_info_t *info) {
 
 static uint64_t kmer_words(uint32_t k) { return k ? 2 * (((1ULL << (2 * (k + 1))) - 4) / 3) : 0; }
 
-static const char kMagic[8] = {'A', 'L', 'N', 'F', 'M', 'I', 'X', '3'};
+static const char kMagic[8] = {'A', 'L', 'N', 'F', 'M', 'I', 'X', '4'};
 
 template <class V>
 static bool write_vec(std::ofstream &f, const V &v) {

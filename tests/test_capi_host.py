@@ -45,7 +45,7 @@ def _read_index_file(path):
     text (n, primary, C[4]) and three length-prefixed u32 vectors."""
     with open(path, "rb") as f:
         data = f.read()
-    assert data[:8] == b"ALNFMIX3"
+    assert data[:8] == b"ALNFMIX4"
     off = 8
     sa_sample, kmer_k, n_seed = struct.unpack_from("<3Q", data, off)
     off += 24
@@ -66,10 +66,14 @@ def _read_index_file(path):
 
 
 def _decode_bwt(t):
+    """Symbols of the saved blocks: per half of a block (96 rows), 3 words of
+    low bits then 3 words of high bits, bit j of word g = the half's symbol
+    32 g + j."""
     b = t["blocks"]
-    words = b[:, 4:]
-    sym = ((words[:, :, None] >> (2 * np.arange(16, dtype=np.uint32))[None, None, :]) & 3).reshape(-1)
-    return sym[: t["n"] + 1].astype(np.uint8)
+    halves = b[:, 4:].reshape(-1, 2, 2, 3)  # block, half, plane, group
+    bits = (halves[..., None] >> np.arange(32, dtype=np.uint32)) & 1  # block, half, plane, group, bit
+    sym = bits[:, :, 0] | (bits[:, :, 1] << 1)  # block, half, group, bit
+    return sym.reshape(-1)[: t["n"] + 1].astype(np.uint8)
 
 
 @pytest.mark.parametrize("name,n,kmer_k,sample", [("iid", 1, 0, 1), ("iid", 191, 3, 4),
