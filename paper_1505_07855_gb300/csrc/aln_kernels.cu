@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) aln_plain_kernel(DIndex X, ReadBatch
 }
 
 #ifndef ALN_PERSISTENT_MIN_BLOCKS
-#define ALN_PERSISTENT_MIN_BLOCKS 5  // 5 resident blocks per SM (with 8 shared stack entries) measured best
+#define ALN_PERSISTENT_MIN_BLOCKS 6  // 6 resident blocks per SM (80 registers, 8 shared stack entries) measured best
 #endif
 
 template <int STACK_CAP>
