@@ -543,7 +543,10 @@ def run_gpu(args):
         "flags": flag_counts,
         "schedule": {"blocks_per_sm": params["persistent"].blocks_per_sm or "max",
                      "autotune_ms": tuned_ms, "graph_replay": bool(graph is not None)},
-        "gpu_launches": args.steps,
+        # per persistent step: D pre-pass, two visit-order kernels, the search
+        # (one launch per step when the step is a graph replay: captured
+        # searches scan D inside the search kernel)
+        "gpu_launches": args.steps * (1 if graph is not None else 4),
         "e2e": {"value": e2e_v, "unit": "reads/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,

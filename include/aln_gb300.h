@@ -116,7 +116,8 @@ int fm_index_load(const char *path, fm_index **out);
 /* Copy the index to device memory (Sec. 2: the whole index is held in GPU
  * memory).  device: CUDA ordinal.  The copy is enqueued on stream and finished
  * before return.  The library allocates the device image (Occ blocks, sampled SA
- * and k-mer table of both texts); ALN_ENOMEM if it does not fit.  Free with
+ * and k-mer table of both texts) and a stream-ordered memory pool for the
+ * search's per-call scratch; ALN_ENOMEM if it does not fit.  Free with
  * fm_dindex_free. */
 int fm_index_to_device(const fm_index *idx, int device, void *stream, fm_dindex **out);
 void fm_dindex_free(fm_dindex *d);
@@ -200,7 +201,13 @@ typedef struct {
  * All arrays are device memory, written asynchronously on stream; the caller
  * synchronises.  Returns ALN_EINVAL for bad params, ALN_EDEVICE on a launch
  * failure, ALN_ELIMIT if the persistent queue did not drain within its bound.
- * Per-read problems are reported in flags, never by the status. */
+ * Per-read problems are reported in flags, never by the status.
+ * Persistent mode first computes every read's D array in a pre-pass and visits
+ * reads in decreasing order of their lower bound; its scratch (256 + 20 bytes
+ * per read) comes from a memory pool owned by the device index, allocated and
+ * freed in stream order by each call.  While stream is being captured into a
+ * graph (or if the pool cannot serve) the search scans D itself and visits
+ * reads in input order.  The results are the same either way. */
 int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
                const aln_params *params, aln_result *out, void *stream);
 

@@ -13,7 +13,9 @@
 namespace aln {
 int persistent_max_blocks(uint32_t z);
 cudaError_t launch_search(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
-                          aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, cudaStream_t st);
+                          aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, void *scratch,
+                          cudaStream_t st);
+uint64_t search_scratch_bytes(uint32_t n);
 }
 
 using namespace aln;
@@ -27,6 +29,7 @@ struct fm_dindex {
     void *mem[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     uint32_t *queues = nullptr;           // persistent-mode queue counters
     std::atomic<uint32_t> next_queue{0};
+    cudaMemPool_t pool = nullptr;         // stream-ordered per-call scratch (D pre-pass, visit order)
 };
 
 static int cuda_fail(cudaError_t e, const char *what) {
@@ -43,6 +46,7 @@ extern "C" void fm_dindex_free(fm_dindex *d) {
         for (void *p : row)
             if (p) cudaFree(p);
     if (d->queues) cudaFree(d->queues);
+    if (d->pool) cudaMemPoolDestroy(d->pool);
     cudaSetDevice(prev);
     delete d;
 }
@@ -91,6 +95,19 @@ extern "C" int fm_index_to_device(const fm_index *idx, int device, void *stream,
         else if ((e = cudaMemsetAsync(d->queues, 0, kQueueSlots * sizeof(uint32_t), st)) != cudaSuccess)
             rc = cuda_fail(e, "fm_index_to_device: memset");
     }
+    if (rc == ALN_OK) {  // optional: without a pool the search scans D in its own loop
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        if (cudaMemPoolCreate(&d->pool, &props) == cudaSuccess) {
+            uint64_t keep = ~0ull;  // keep freed scratch for the next call
+            cudaMemPoolSetAttribute(d->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        } else {
+            cudaGetLastError();
+            d->pool = nullptr;
+        }
+    }
     if (rc == ALN_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "fm_index_to_device: sync");
     cudaSetDevice(prev);
     if (rc != ALN_OK) {
@@ -133,8 +150,26 @@ extern "C" int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != idx->device) cudaSetDevice(idx->device);
-    cudaError_t e = launch_search(idx->X, rb, n_reads, sp, out->reads, out->hits, P.mode, queue,
-                                  static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Persistent mode takes a per-call scratch from the index's pool, ordered on
+    // the stream (so concurrent calls never share it).  While the stream is being
+    // captured into a graph, or if the pool cannot serve, the search scans D
+    // itself and visits reads in input order: same results.
+    void *scratch = nullptr;
+    if (P.mode == ALN_MODE_PERSISTENT && n_reads && d->pool) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            cs = cudaStreamCaptureStatusActive;
+        }
+        if (cs == cudaStreamCaptureStatusNone &&
+            cudaMallocFromPoolAsync(&scratch, search_scratch_bytes(n_reads), d->pool, st) != cudaSuccess) {
+            cudaGetLastError();
+            scratch = nullptr;
+        }
+    }
+    cudaError_t e = launch_search(idx->X, rb, n_reads, sp, out->reads, out->hits, P.mode, queue, scratch, st);
+    if (scratch) cudaFreeAsync(scratch, st);
     if (prev != idx->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(e, "aln_search: launch");
     return ALN_OK;
@@ -334,7 +369,7 @@ extern "C" int aln_search_noalloc(const fm_dindex *idx, const aln_batch *batch, 
     int rc = noalloc_scratch(idx->device, &scratch);
     if (rc == ALN_OK) {
         // launch_search clears the queue counter (scratch[0]) on the stream first
-        cudaError_t e = launch_search(idx->X, rb, n_reads, sp, out->reads, out->hits, ALN_MODE_PERSISTENT, scratch,
+        cudaError_t e = launch_search(idx->X, rb, n_reads, sp, out->reads, out->hits, ALN_MODE_PERSISTENT, scratch, nullptr,
                                       static_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) rc = cuda_fail(e, "aln_search_noalloc: launch");
     }

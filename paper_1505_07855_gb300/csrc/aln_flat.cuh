@@ -277,7 +277,8 @@ struct FlatLane {
     // (fills fr) or is done.  Each round does O(1) work; the rounds are bounded.
     __device__ __forceinline__ void control(const DIndex &X, const ReadBatch &rb, uint32_t n_reads,
                                             const SearchParams &p, aln_read_result *res, aln_hit *hits,
-                                            uint32_t *queue, uint32_t *sb, uint32_t *sn, FetchReq &fr) {
+                                            uint32_t *queue, const uint32_t *order, const uint2 *dbp,
+                                            uint32_t *sb, uint32_t *sn, FetchReq &fr) {
         const uint32_t n = X.t[0].n;  // both texts have the same length
         fr.kind = F_NONE;
         for (int round = 0; round < 32; round++) {
@@ -295,6 +296,7 @@ struct FlatLane {
                     phase = PH_FREE;
                     return;
                 }
+                if (order) r = order[r];
                 role = ROLE_OWN;
                 rv = own_rv;
                 m = rb.len[r];
@@ -309,6 +311,22 @@ struct FlatLane {
                     continue;
                 }
                 load_read(rb, rb.offset[r], m, sb, sn);
+                if (dbp) {  // D from the pre-pass: go straight to the first pass
+                    const uint2 a = dbp[2ull * r], b = dbp[2ull * r + 1];
+                    bpa0 = a.x;
+                    bpa1 = a.y;
+                    bpb0 = b.x;
+                    bpb1 = b.y;
+                    d00 = d_at(bpa0, bpa1, 0);
+                    d01 = d_at(bpb0, bpb1, 0);
+                    const uint32_t lb = min(d00, d01);
+                    if (lb > z) {
+                        write_result(res, hits, p, false, 0);
+                        continue;
+                    }
+                    start_pass(n, p.strata == ALN_STRATA_FULL ? z : min(z, lb + 1));
+                    continue;
+                }
                 phase = PH_DSCAN;
                 s = 0;
                 dj = static_cast<int>(m) - 1;

@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(kThreads) aln_plain_kernel(DIndex X, ReadBatch
 template <int STACK_CAP>
 __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persistent_kernel(DIndex X, ReadBatch rb, uint32_t n_reads,
                                                                   SearchParams p, aln_read_result *res,
-                                                                  aln_hit *hits, uint32_t *queue) {
+                                                                  aln_hit *hits, uint32_t *queue,
+                                                                  const uint32_t *order, const uint2 *dbp) {
     __shared__ uint32_t s_bases[kReadWords * kThreads];
     __shared__ uint32_t s_nmask[kMaskWords * kThreads];
     __shared__ uint4 s_stack[kSmemStack * kThreads];
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
 #ifdef ALN_STATS
         const unsigned long long k0 = clock64();
 #endif
-        L.control(X, rb, n_reads, p, res, hits, queue, sb, sn, fr);
+        L.control(X, rb, n_reads, p, res, hits, queue, order, dbp, sb, sn, fr);
         __syncwarp();
 #ifdef ALN_STATS
         const unsigned long long k1 = clock64();
@@ -153,12 +154,81 @@ cudaError_t debug_stats(unsigned long long *out, int reset) {
 }
 #endif
 
+// D-array pre-pass.  Thread t runs the greedy D scan of strand t & 1 of read
+// t >> 1 on that strand's other index (strand 0 on X, strand 1 on X reversed)
+// and stores its breakpoints; reads the search would flag before any scan get
+// zeros.  The persistent search then starts from these instead of scanning.
+__global__ void __launch_bounds__(kThreads) aln_dscan_kernel(DIndex X, ReadBatch rb, uint32_t n, SearchParams p,
+                                                             uint2 *dbp) {
+    __shared__ uint32_t s_bases[kReadWords * kThreads];
+    __shared__ uint32_t s_nmask[kMaskWords * kThreads];
+    const uint64_t t = static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    if (t >= 2ull * n) return;
+    const uint32_t r = static_cast<uint32_t>(t >> 1), s = static_cast<uint32_t>(t & 1u);
+    const uint32_t m = rb.len[r];
+    const uint32_t z = rb.z ? rb.z[r] : p.z;
+    uint2 out = make_uint2(0u, 0u);
+    if (m >= 1 && m <= ALN_MAX_READ_LEN && z <= ALN_MAX_Z && z <= p.z) {
+        uint32_t *sb = s_bases + threadIdx.x, *sn = s_nmask + threadIdx.x;
+        load_read(rb, rb.offset[r], m, sb, sn);
+        const ReadView rv{sb, sn};
+        d_scan(X.t[s], rv, m, s, min(z + 1, 8u), out.x, out.y);
+    }
+    dbp[t] = out;
+}
+
+// Visit order for the persistent search: reads by decreasing lower bound
+// D(0) = min over strands (0..8), so that the lanes of a warp tend to run the
+// same number of deepening passes.  Counting sort in two launches; the order
+// inside one bound is arbitrary (a read's result does not depend on it).
+constexpr uint32_t kOrderBins = 16;
+
+__device__ __forceinline__ uint32_t order_key(const uint2 *dbp, uint32_t r) {
+    const uint2 a = dbp[2ull * r], b = dbp[2ull * r + 1];
+    return min(d_at(a.x, a.y, 0), d_at(b.x, b.y, 0));
+}
+
+__global__ void aln_order_count_kernel(const uint2 *dbp, uint32_t n, uint32_t *counts) {
+    __shared__ uint32_t h[kOrderBins];
+    if (threadIdx.x < kOrderBins) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint64_t r = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        atomicAdd(&h[order_key(dbp, static_cast<uint32_t>(r))], 1u);
+    __syncthreads();
+    if (threadIdx.x < kOrderBins && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void aln_order_scatter_kernel(const uint2 *dbp, uint32_t n, const uint32_t *counts, uint32_t *cursor,
+                                         uint32_t *order) {
+    __shared__ uint32_t first[kOrderBins];
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int k = kOrderBins - 1; k >= 0; k--) {  // largest bound first
+            first[k] = acc;
+            acc += counts[k];
+        }
+    }
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint64_t r = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t key = order_key(dbp, static_cast<uint32_t>(r));
+        const unsigned grp = __match_any_sync(__activemask(), key);  // lanes with the same bound
+        const uint32_t leader = __ffs(grp) - 1;
+        uint32_t off = 0;
+        if (lane == leader) off = atomicAdd(&cursor[key], static_cast<uint32_t>(__popc(grp)));
+        off = __shfl_sync(grp, off, leader);
+        order[first[key] + off + __popc(grp & ((1u << lane) - 1u))] = static_cast<uint32_t>(r);
+    }
+}
+
 int stack_cap_for(uint32_t z) { return z <= 2 ? 19 : (z <= 4 ? 37 : 64); }
 
 template <int CAP>
 static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
                               aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue,
-                              cudaStream_t st) {
+                              void *scratch, cudaStream_t st) {
     if (mode == ALN_MODE_PLAIN) {
         const uint32_t blocks = (n + kThreads - 1) / kThreads;
         aln_plain_kernel<CAP><<<blocks, kThreads, 0, st>>>(X, rb, n, p, res, hits);
@@ -173,7 +243,20 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
         const uint32_t need = (n + kThreads - 1) / kThreads;
         if (blocks > need) blocks = need ? need : 1;
         cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
-        aln_persistent_kernel<CAP><<<blocks, kThreads, 0, st>>>(X, rb, n, p, res, hits, queue);
+        uint2 *dbp = nullptr;
+        uint32_t *order = nullptr;
+        if (scratch) {  // D pre-pass and visit order (layout: search_scratch_bytes)
+            uint32_t *counts = static_cast<uint32_t *>(scratch), *cursor = counts + kOrderBins;
+            dbp = reinterpret_cast<uint2 *>(static_cast<char *>(scratch) + 256);
+            order = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + 256 + 16ull * n);
+            cudaMemsetAsync(scratch, 0, 2 * kOrderBins * sizeof(uint32_t), st);
+            aln_dscan_kernel<<<static_cast<unsigned>((2ull * n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+                X, rb, n, p, dbp);
+            const uint32_t ob = min((n + 255u) / 256u, static_cast<uint32_t>(sms) * 8u);
+            aln_order_count_kernel<<<ob, 256, 0, st>>>(dbp, n, counts);
+            aln_order_scatter_kernel<<<ob, 256, 0, st>>>(dbp, n, counts, cursor, order);
+        }
+        aln_persistent_kernel<CAP><<<blocks, kThreads, 0, st>>>(X, rb, n, p, res, hits, queue, order, dbp);
     }
     return cudaGetLastError();
 }
@@ -189,13 +272,18 @@ int persistent_max_blocks(uint32_t z) {
     return per_sm;
 }
 
+// Bytes of the optional persistent-mode scratch for n reads: order-sort counters
+// (256 B), D breakpoints (2 x 8 B per read), visit order (4 B per read).
+uint64_t search_scratch_bytes(uint32_t n) { return 256ull + 20ull * n; }
+
 cudaError_t launch_search(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
-                          aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, cudaStream_t st) {
+                          aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, void *scratch,
+                          cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     switch (stack_cap_for(p.z)) {
-        case 19: return launch_cap<19>(X, rb, n, p, res, hits, mode, queue, st);
-        case 37: return launch_cap<37>(X, rb, n, p, res, hits, mode, queue, st);
-        default: return launch_cap<64>(X, rb, n, p, res, hits, mode, queue, st);
+        case 19: return launch_cap<19>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        case 37: return launch_cap<37>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        default: return launch_cap<64>(X, rb, n, p, res, hits, mode, queue, scratch, st);
     }
 }
 
