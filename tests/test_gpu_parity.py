@@ -11,7 +11,7 @@ from synth import Rng, Reads, reference_iid, simulate_reads, workload, z_for_len
 pytestmark = pytest.mark.gpu
 
 MODES = [aln.MODE_PLAIN, aln.MODE_PERSISTENT]
-BENCH_KMER = 11  # prefix-trie depth the benchmark uses
+BENCH_KMER = 10  # prefix-trie depth the benchmark uses
 
 
 @pytest.fixture(scope="module")
