@@ -228,7 +228,9 @@ class Aligner:
     def capture(self, d, params: Params, res, hits):
         """Capture one search of the uploaded batch d into a CUDA graph; replay it
         with graph.replay() for every new batch copied into the same buffers.
-        One replay at a time (the graph's queue counter is fixed)."""
+        One replay at a time (the graph's queue counter is fixed).  A captured
+        persistent search scans D inside the search kernel and visits reads in
+        input order (no per-call scratch); its results are those of aln_search."""
         t = self.torch
         side = t.cuda.Stream(device=self.dev)
         side.wait_stream(t.cuda.current_stream(self.dev))
