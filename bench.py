@@ -343,6 +343,18 @@ def accuracy_report(w, outp, pos, npos, hit_cap, valid):
     return out
 
 
+def workload_config(name, w, n_per_step, ws, mode="persistent"):
+    """The JSON line's config: the workload by name and sizes, the limits."""
+    lim = w.params
+    mixed = name == "human_mixed"
+    return {"workload": name, "ref_bp": int(w.text.size), "reads_per_step": int(n_per_step),
+            "read_len": "36-250 mixed" if mixed else int(w.reads.lens[0]) if w.reads.n else 0,
+            "z": "min(6, ceil(0.04 len))" if mixed else lim["z"], "seed": [lim["seed_len"], lim["seed_z"]],
+            "strata": "BEST1", "mode": mode,
+            "l2": "flushed (512 MiB write) before every step" if mode == "persistent" else "n/a (CPU)",
+            "parallelism": f"replicas{ws}" if ws > 1 else "single"}
+
+
 def run_reference(args):
     """CPU oracle arm: each step aligns a bounded seeded sample on all host cores."""
     ws, rank, _ = _dist()
@@ -375,7 +387,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "reads/s", "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "config": {"workload": args.workload, "reads_per_step": per_step},
+        "data": "synthetic", "config": workload_config(args.workload, w, per_step, 1, mode="oracle (CPU)"),
         "cpu_baseline": {"value": v, "unit": "reads/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -533,11 +545,7 @@ def run_gpu(args):
         "metric": METRIC, "value": ws * n / (ms_head / 1000), "unit": "reads/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_head, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": args.workload, "ref_bp": int(w.text.size), "reads_per_step": n,
-                   "read_len": "36-250 mixed" if per_read_z else 100,
-                   "z": "min(6, ceil(0.04 len))" if per_read_z else lim["z"], "seed": [lim["seed_len"], lim["seed_z"]],
-                   "strata": "BEST1", "mode": "persistent", "l2": "flushed (512 MiB write) before every step",
-                   "parallelism": f"replicas{ws}" if ws > 1 else "single"},
+        "config": workload_config(args.workload, w, n, ws),
         "plain": {"value": ws * n / (ms_plain / 1000), "ms_per_step": ms_plain,
                   "bit_identical_to_persistent_on_complete_reads": same},
         "flags": flag_counts,

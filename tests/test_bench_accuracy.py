@@ -1,7 +1,7 @@
 """The bench's placement report (best stratum against the simulated origin),
 driven by the oracle's hits and positions on a small workload: error-bounded
 reads of a repeat-free i.i.d. text place at their origin, and a truth shifted
-beyond the tolerance places none."""
+beyond the tolerance places none.  Both bench arms describe the same workload."""
 import numpy as np
 import pytest
 
@@ -38,3 +38,12 @@ def test_shifted_truth_places_none():
     w = workload("tiny36", ref_len=200_000, n_reads=400, seed=12)
     w.reads.true_pos = w.reads.true_pos + 1000
     assert _report(w)["best_covers_origin"] == 0.0
+
+
+def test_both_bench_arms_name_the_same_workload():
+    w = workload("chr100", ref_len=300_000, n_reads=50, seed=1)
+    gpu = bench.workload_config("chr100", w, w.reads.n, 1)
+    ref = bench.workload_config("chr100", w, 20, 1, mode="oracle (CPU)")
+    same = ("workload", "ref_bp", "read_len", "z", "seed", "strata", "parallelism")
+    assert {k: gpu[k] for k in same} == {k: ref[k] for k in same}
+    assert gpu["read_len"] == 100 and gpu["z"] == 4 and gpu["seed"] == [32, 2]
