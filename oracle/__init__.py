@@ -55,7 +55,7 @@ def lib():
         L = ctypes.CDLL(build())
         P, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
         L.orc_build.restype = P
-        L.orc_build.argtypes = [P, u64, u64, i32]
+        L.orc_build.argtypes = [P, u64, u64, i32, i32]
         L.orc_free.argtypes = [P]
         L.orc_n.restype = u64
         L.orc_n.argtypes = [P]
@@ -71,10 +71,17 @@ def lib():
         L.orc_align.argtypes = [P, P, P, P, P, u64, ctypes.POINTER(_Params), i32, P, P, P]
         L.orc_dscan.restype = i32
         L.orc_dscan.argtypes = [P, i32, P, i32, P]
+        L.orc_mix64.restype = u64
+        L.orc_mix64.argtypes = [u64]
         L.orc_positions.restype = i32
         L.orc_positions.argtypes = [P, P, u64, ctypes.c_uint32, P, P]
         _lib = L
     return _lib
+
+
+def mix64(x: int) -> int:
+    """The oracle's SplitMix64 output function on state x + 0x9E3779B97F4A7C15."""
+    return int(lib().orc_mix64(x & 0xFFFFFFFFFFFFFFFF))
 
 
 def _ptr(a: np.ndarray):
@@ -86,13 +93,15 @@ def default_threads() -> int:
 
 
 class OracleIndex:
-    """Index of X (which=0) and of X reversed (which=1), built by naive suffix sort."""
+    """Index of X (which=0) and of X reversed (which=1), built by naive suffix sort.
+    ``bucket_k``: leading symbols the sort groups suffixes by before sorting each
+    group with the byte-wise comparator (0 = chosen from the text length)."""
 
-    def __init__(self, text: np.ndarray, n_seed: int = 0, threads: int | None = None):
+    def __init__(self, text: np.ndarray, n_seed: int = 0, threads: int | None = None, bucket_k: int = 0):
         text = np.ascontiguousarray(text, dtype=np.uint8)
         self._text_keep = text
         self.threads = threads or default_threads()
-        h = lib().orc_build(_ptr(text), text.size, n_seed, self.threads)
+        h = lib().orc_build(_ptr(text), text.size, n_seed, self.threads, bucket_k)
         if not h:
             raise MemoryError("oracle index build failed")
         self._h = h

@@ -72,6 +72,9 @@ static uint64_t mix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
+/* The mix function itself (exported for its pin against published outputs). */
+uint64_t orc_mix64(uint64_t x) { return mix64(x); }
+
 /* ------------------------------------------------------------ suffix sort */
 
 static const uint8_t *g_sort_text;
@@ -92,76 +95,138 @@ static int qsort_cmp(const void *a, const void *b)
     return suffix_cmp(*(const uint32_t *)a, *(const uint32_t *)b);
 }
 
-typedef struct { uint32_t *a; uint64_t len; } sort_job;
-
-static void *sort_worker(void *p)
+/* Bucket of suffix i: its first bk symbols as a base-4 number, a suffix shorter
+ * than bk symbols padded with A (code 0).  Such a short suffix is smaller than
+ * every other suffix of its bucket (they all continue it, and $ is the smallest
+ * symbol), and the bucket order agrees with the suffix order otherwise, so
+ * sorting every bucket with the comparator gives the order of one global sort. */
+static uint64_t bucket_of(const uint8_t *text, uint64_t n, uint64_t i, int bk)
 {
-    sort_job *j = (sort_job *)p;
-    qsort(j->a, j->len, sizeof(uint32_t), qsort_cmp);
+    uint64_t key = 0;
+    for (int j = 0; j < bk; j++) key = 4 * key + (i + j < n ? text[i + j] : 0);
+    return key;
+}
+
+typedef struct {
+    const uint8_t *text;
+    uint64_t n, lo, hi;     /* suffix starts [lo, hi) of this thread */
+    int bk;
+    uint32_t *count;        /* per-thread bucket counts, then write cursors */
+    uint32_t *out;
+} scatter_job;
+
+static void *count_worker(void *p)
+{
+    scatter_job *j = (scatter_job *)p;
+    for (uint64_t i = j->lo; i < j->hi; i++) j->count[bucket_of(j->text, j->n, i, j->bk)]++;
     return NULL;
 }
 
-typedef struct { const uint32_t *a; uint64_t na; const uint32_t *b; uint64_t nb; uint32_t *out; } merge_job;
-
-static void *merge_worker(void *p)
+static void *scatter_worker(void *p)
 {
-    merge_job *j = (merge_job *)p;
-    uint64_t x = 0, y = 0, o = 0;
-    while (x < j->na && y < j->nb)
-        j->out[o++] = (suffix_cmp(j->a[x], j->b[y]) <= 0) ? j->a[x++] : j->b[y++];
-    while (x < j->na) j->out[o++] = j->a[x++];
-    while (y < j->nb) j->out[o++] = j->b[y++];
+    scatter_job *j = (scatter_job *)p;
+    for (uint64_t i = j->lo; i < j->hi; i++) {
+        uint64_t b = bucket_of(j->text, j->n, i, j->bk);
+        j->out[j->count[b]++] = (uint32_t)i;
+    }
     return NULL;
 }
 
-/* Naive suffix sort of text$ (text of length n): qsort of all suffix starts
- * with the byte-wise comparator, split over threads and merged pairwise. */
-static int naive_sa(const uint8_t *text, uint64_t n, uint32_t *sa, int nthreads)
+typedef struct {
+    uint32_t *a;            /* suffix starts, grouped by bucket */
+    const uint64_t *start;  /* bucket b is a[start[b] .. start[b+1]-1] */
+    uint64_t n_buckets, next;
+    pthread_mutex_t *mu;
+} bucket_job;
+
+static void *bucket_sort_worker(void *p)
+{
+    bucket_job *j = (bucket_job *)p;
+    for (;;) {
+        pthread_mutex_lock(j->mu);
+        uint64_t b0 = j->next, b1 = b0 + 1024 < j->n_buckets ? b0 + 1024 : j->n_buckets;
+        j->next = b1;
+        pthread_mutex_unlock(j->mu);
+        if (b0 >= j->n_buckets) break;
+        for (uint64_t b = b0; b < b1; b++) {
+            uint64_t len = j->start[b + 1] - j->start[b];
+            if (len > 1) qsort(j->a + j->start[b], len, sizeof(uint32_t), qsort_cmp);
+        }
+    }
+    return NULL;
+}
+
+/* Naive suffix sort of text$ (text of length n): suffix starts grouped by their
+ * first bk symbols (bk = 0: chosen from n), then every group sorted by qsort
+ * with the byte-wise comparator, groups in parallel. */
+static int naive_sa(const uint8_t *text, uint64_t n, uint32_t *sa, int nthreads, int bk)
 {
     g_sort_text = text;
     g_sort_n = n;
     sa[0] = (uint32_t)n;                 /* the suffix "$" is the smallest */
-    uint32_t *a = sa + 1;
-    for (uint64_t i = 0; i < n; i++) a[i] = (uint32_t)i;
+    if (n == 0) return 0;
+    if (bk <= 0) {                       /* about 64 suffixes per bucket, 1..12 symbols */
+        bk = 1;
+        while (bk < 12 && ((uint64_t)1 << (2 * bk)) * 64 < n) bk++;
+    }
+    if (bk > 12) bk = 12;
+    uint64_t nb = (uint64_t)1 << (2 * bk);
     if (nthreads < 1) nthreads = 1;
     if ((uint64_t)nthreads > n / 4096 + 1) nthreads = (int)(n / 4096 + 1);
-    int parts = 1;
-    while (parts * 2 <= nthreads) parts *= 2;
-    uint64_t *bnd = (uint64_t *)malloc((parts + 1) * sizeof(uint64_t));
-    for (int p = 0; p <= parts; p++) bnd[p] = n * (uint64_t)p / parts;
-    pthread_t *th = (pthread_t *)malloc(parts * sizeof(pthread_t));
-    sort_job *sj = (sort_job *)malloc(parts * sizeof(sort_job));
-    for (int p = 0; p < parts; p++) {
-        sj[p].a = a + bnd[p];
-        sj[p].len = bnd[p + 1] - bnd[p];
-        pthread_create(&th[p], NULL, sort_worker, &sj[p]);
+    while (nthreads > 1 && (uint64_t)nthreads * nb * sizeof(uint32_t) > ((uint64_t)2 << 30)) nthreads--;
+    uint32_t *count = (uint32_t *)calloc((uint64_t)nthreads * nb, sizeof(uint32_t));
+    uint64_t *start = (uint64_t *)malloc((nb + 1) * sizeof(uint64_t));
+    pthread_t *th = (pthread_t *)malloc(nthreads * sizeof(pthread_t));
+    scatter_job *sj = (scatter_job *)malloc(nthreads * sizeof(scatter_job));
+    if (!count || !start || !th || !sj) return -1;
+    for (int t = 0; t < nthreads; t++) {
+        sj[t].text = text; sj[t].n = n; sj[t].bk = bk; sj[t].out = sa + 1;
+        sj[t].lo = n * (uint64_t)t / nthreads;
+        sj[t].hi = n * (uint64_t)(t + 1) / nthreads;
+        sj[t].count = count + (uint64_t)t * nb;
+        pthread_create(&th[t], NULL, count_worker, &sj[t]);
     }
-    for (int p = 0; p < parts; p++) pthread_join(th[p], NULL);
-    uint32_t *tmp = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
-    if (!tmp) return -1;
-    uint32_t *src = a, *dst = tmp;
-    merge_job *mj = (merge_job *)malloc(parts * sizeof(merge_job));
-    for (int width = 1; width < parts; width *= 2) {
-        int jobs = 0;
-        for (int p = 0; p < parts; p += 2 * width) {
-            uint64_t lo = bnd[p], mid = bnd[p + width], hi = bnd[p + 2 * width];
-            mj[jobs].a = src + lo; mj[jobs].na = mid - lo;
-            mj[jobs].b = src + mid; mj[jobs].nb = hi - mid;
-            mj[jobs].out = dst + lo;
-            pthread_create(&th[jobs], NULL, merge_worker, &mj[jobs]);
-            jobs++;
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    /* bucket b starts after all smaller buckets; thread t writes after threads < t */
+    uint64_t acc = 0;
+    for (uint64_t b = 0; b < nb; b++) {
+        start[b] = acc;
+        for (int t = 0; t < nthreads; t++) {
+            uint32_t c = count[(uint64_t)t * nb + b];
+            count[(uint64_t)t * nb + b] = (uint32_t)acc;  /* cursor (acc < n < 2^32) */
+            acc += c;
         }
-        for (int q = 0; q < jobs; q++) pthread_join(th[q], NULL);
-        uint32_t *s = src; src = dst; dst = s;
     }
-    if (src != a) memcpy(a, src, n * sizeof(uint32_t));
-    free(tmp); free(mj); free(sj); free(th); free(bnd);
+    start[nb] = acc;
+    for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, scatter_worker, &sj[t]);
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    free(count);
+    pthread_mutex_t mu;
+    pthread_mutex_init(&mu, NULL);
+    bucket_job bj = {sa + 1, start, nb, 0, &mu};
+    for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, bucket_sort_worker, &bj);
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&mu);
+    free(start); free(th); free(sj);
     return 0;
 }
 
 /* ------------------------------------------------------------ index */
 
-static int build_text(otext *t, const uint8_t *codes, uint64_t n, int nthreads)
+typedef struct { const otext *t; uint64_t lo, hi; uint8_t *bwt; } bwt_job;
+
+/* B[r] = Y[SA[r]-1], or $ where SA[r] = 0, for rows [lo, hi) */
+static void *bwt_worker(void *p)
+{
+    bwt_job *j = (bwt_job *)p;
+    for (uint64_t r = j->lo; r < j->hi; r++) {
+        uint32_t s = j->t->sa[r];
+        j->bwt[r] = s == 0 ? SYM_DOLLAR : j->t->text[s - 1];
+    }
+    return NULL;
+}
+
+static int build_text(otext *t, const uint8_t *codes, uint64_t n, int nthreads, int bk)
 {
     t->n = n;
     t->text = (uint8_t *)malloc(n ? n : 1);
@@ -171,13 +236,20 @@ static int build_text(otext *t, const uint8_t *codes, uint64_t n, int nthreads)
     t->ck = (uint32_t *)calloc(4 * nck, sizeof(uint32_t));
     if (!t->text || !t->sa || !t->bwt || !t->ck) return -1;
     memcpy(t->text, codes, n);
-    if (naive_sa(t->text, n, t->sa, nthreads)) return -1;
-    /* B[r] = Y[SA[r]-1], or $ where SA[r] = 0 */
-    for (uint64_t r = 0; r <= n; r++) {
-        uint32_t s = t->sa[r];
-        if (s == 0) { t->bwt[r] = SYM_DOLLAR; t->primary = r; }
-        else t->bwt[r] = t->text[s - 1];
+    if (naive_sa(t->text, n, t->sa, nthreads, bk)) return -1;
+    int nt = nthreads < 1 ? 1 : nthreads;
+    pthread_t th[256];
+    bwt_job bj[256];
+    if (nt > 256) nt = 256;
+    for (int q = 0; q < nt; q++) {
+        bj[q].t = t; bj[q].bwt = t->bwt;
+        bj[q].lo = (n + 1) * (uint64_t)q / nt;
+        bj[q].hi = (n + 1) * (uint64_t)(q + 1) / nt;
+        pthread_create(&th[q], NULL, bwt_worker, &bj[q]);
     }
+    for (int q = 0; q < nt; q++) pthread_join(th[q], NULL);
+    for (uint64_t r = 0; r <= n; r++)
+        if (t->bwt[r] == SYM_DOLLAR) t->primary = r;
     /* C[c] = number of symbols smaller than c in Y */
     uint64_t cnt[4] = {0, 0, 0, 0};
     for (uint64_t i = 0; i < n; i++) cnt[t->text[i]]++;
@@ -213,7 +285,10 @@ static int lf_extend(const otext *t, int c, uint64_t k, uint64_t l, uint64_t *k2
     return a <= b;
 }
 
-orc_index *orc_build(const uint8_t *codes, uint64_t n, uint64_t n_seed, int nthreads)
+/* Index of X and of Xr.  bucket_k: leading symbols the suffix sort groups by
+ * before sorting each group (0 = chosen from n); the suffix array does not
+ * depend on it. */
+orc_index *orc_build(const uint8_t *codes, uint64_t n, uint64_t n_seed, int nthreads, int bucket_k)
 {
     if (n >= 0xFFFFFFFFULL) return NULL;
     orc_index *ix = (orc_index *)calloc(1, sizeof(orc_index));
@@ -224,7 +299,8 @@ orc_index *orc_build(const uint8_t *codes, uint64_t n, uint64_t n_seed, int nthr
     for (uint64_t i = 0; i < n; i++)
         x[i] = codes[i] < 4 ? codes[i] : (uint8_t)(mix64(n_seed ^ i) & 3);
     for (uint64_t i = 0; i < n; i++) xr[i] = x[n - 1 - i];
-    if (build_text(&ix->t[0], x, n, nthreads) || build_text(&ix->t[1], xr, n, nthreads)) return NULL;
+    if (build_text(&ix->t[0], x, n, nthreads, bucket_k) || build_text(&ix->t[1], xr, n, nthreads, bucket_k))
+        return NULL;
     free(x);
     free(xr);
     return ix;

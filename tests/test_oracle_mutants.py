@@ -26,6 +26,9 @@ MUTANTS = {
     "c1_stratum": ("all[i].n_diff == d_best + 1", "all[i].n_diff == d_best + 2"),
     "reverse_not_complemented": ("(strand ? (uint8_t)(3 - b) : b)", "b"),
     "dscan_overcounts": ("            cnt++;\n", "            cnt += 2;\n"),
+    "bucket_pads_with_t": ("key = 4 * key + (i + j < n ? text[i + j] : 0);", "key = 4 * key + (i + j < n ? text[i + j] : 3);"),
+    "bucket_key_drops_symbol": ("for (int j = 0; j < bk; j++) key", "for (int j = 1; j < bk; j++) key"),
+    "mix64_shift": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
     "dollar_largest": ("return li < lj ? -1 : (li > lj ? 1 : 0);", "return li > lj ? -1 : (li < lj ? 1 : 0);"),
     "best1_no_second_stratum": ("int keep_max = (p->strata == 1) ? z : (d_best + 1 <= z ? d_best + 1 : z);",
                                 "int keep_max = (p->strata == 1) ? z : d_best;"),
@@ -41,7 +44,8 @@ def _pin_calls():
     c = pins.CASES
     return [
         pins.test_hand_example,
-        lambda: pins.test_sa_bwt_against_naive_sort(300, 4, 2),
+        pins.test_mix64_matches_published_splitmix64,
+        lambda: pins.test_sa_bwt_against_naive_sort(300, 4, 2, 3),
         lambda: pins.test_exact_interval_is_naive_scan(21),
         pins.test_z0_is_exact_matching,
         lambda: pins.test_mismatch_only_is_hamming_scan(2),

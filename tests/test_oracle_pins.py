@@ -75,11 +75,15 @@ def _rand_text(n, seed, alphabet=4):
     return t
 
 
+@pytest.mark.parametrize("bucket_k", [0, 3, 12])
 @pytest.mark.parametrize("n,seed,alpha", [(1, 1, 4), (2, 2, 4), (57, 3, 4), (300, 4, 2),
                                           (1000, 5, 4), (777, 6, 1)])
-def test_sa_bwt_against_naive_sort(n, seed, alpha):
+def test_sa_bwt_against_naive_sort(n, seed, alpha, bucket_k):
+    """Suffix arrays against Python's sort of the suffix strings, whatever the
+    number of leading symbols the oracle's sort groups by first (suffixes shorter
+    than the group key included)."""
     t = _rand_text(n, seed, alpha)
-    ix = oracle.OracleIndex(t, threads=4)
+    ix = oracle.OracleIndex(t, threads=4, bucket_k=bucket_k)
     s = codes_to_str(t)
     assert ix.sa(0).tolist() == brute.naive_sa(s)
     assert ix.sa(1).tolist() == brute.naive_sa(s[::-1])
@@ -361,6 +365,30 @@ def test_n_in_reference_replaced_by_splitmix():
     exp[t == 4] = (mix64(np.uint64(12345) ^ pos) & np.uint64(3)).astype(np.uint8)
     assert np.array_equal(ix.text(0), exp)
     assert np.array_equal(ix.text(1), exp[::-1])
+
+
+def _splitmix_vectors():
+    out = []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "splitmix64.txt")):
+        f = line.split()
+        if f and f[0] == "seed":
+            out.append((int(f[1]), [int(x) for x in f[2:]]))
+    return out
+
+
+def test_mix64_matches_published_splitmix64():
+    """The oracle's and the input generator's mix64 give SplitMix64's published
+    outputs: output i of a generator seeded with s is mix64(s + i * golden)."""
+    G = 0x9E3779B97F4A7C15
+    vecs = _splitmix_vectors()
+    assert len(vecs) == 2
+    for seed, outs in vecs:
+        for i, v in enumerate(outs):
+            st = (seed + i * G) & 0xFFFFFFFFFFFFFFFF
+            assert oracle.mix64(st) == v
+            assert mix64(st) == v
+        arr = mix64(np.array([(seed + i * G) & 0xFFFFFFFFFFFFFFFF for i in range(len(outs))], np.uint64))
+        assert arr.tolist() == outs
 
 
 EDIT_LIMITS = [
