@@ -29,11 +29,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "reads/s bit-exact vs oracle (batched vs plain, 1 GB300); % HBM roofline; p99 ms"
 BYTES_PER_LOOKUP = 64
-# DRAM bytes (read + write) of aln_persistent_kernel from one ncu capture of the
-# chr100 workload (300 000 reads, scaled per read; profiles/aln_persistent_chr100.md).
-# Used only while the kernel sources hash to the value they had at capture time.
+# DRAM bytes (read + write) of aln_persistent_kernel per read from one ncu capture
+# of each workload (a few hundred thousand reads, scaled per read; the profile
+# summaries under profiles/ give the command).  Used only while the kernel
+# sources hash to the value they had at capture time.
 KERNEL_SOURCES = ("aln_device.cuh", "aln_search.cuh", "aln_flat.cuh", "aln_kernels.cu")
-TRAFFIC_CAPTURE = {"src_sha256_16": "8019f3912031bb9f", "workload": "chr100", "dram_bytes_per_read": 25414.0}
+TRAFFIC_CAPTURE = {}  # workload -> {"src_sha256_16": ..., "dram_bytes_per_read": ...}
+L2_BYTES = 126 << 20  # GB300 L2 (cudaDevAttrL2CacheSize reports 126 MiB)
 
 
 def _src_hash() -> str:
@@ -160,7 +162,7 @@ def oracle_sample(w, n_sample, threads, seed=7):
     return ox, idx, ro, ho, look, t_index, t_align
 
 
-def serving_phase(aln, dix, w, lam, seconds, seed=5):
+def serving_phase(aln, dix, w, lam, seconds, seed=5, text_note="the 100 Mbp bench text stands in for the 3.1 Gbp one"):
     """Poisson request stream on the resident index: request sizes log-uniform on
     [1, 100000] reads, lengths uniform over 50..250 bp, z = min(6, ceil(0.04 len)),
     errors as the tiny36 recipe; reads are cut from a pre-simulated pool."""
@@ -223,8 +225,7 @@ def serving_phase(aln, dix, w, lam, seconds, seed=5):
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p95_ms": float(np.percentile(lat, 95)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
-            "batches": st["batches"], "slots": st["n_slots"],
-            "text": "the 100 Mbp bench text stands in for the 3.1 Gbp one"}
+            "batches": st["batches"], "slots": st["n_slots"], "text": text_note}
 
 
 def _levenshtein(a, b):
@@ -284,10 +285,11 @@ def property_checks(w, outp, pos, npos, hit_cap, n_hits, valid, n_sample=400, se
             "origin_recall": found / max(1, eligible)}
 
 
-def gather_probe_phase(aln, torch, dev, stream, buf_gib=4, n_gathers=1 << 27, best_of=10, warmup=3):
-    """Random 64-byte block-read rate over a buffer far larger than L2 (best of
-    best_of launches, CUDA events on the launching stream)."""
-    buf = torch.empty(buf_gib << 30, dtype=torch.uint8, device=dev)
+def gather_probe_phase(aln, torch, dev, stream, buf_bytes=4 << 30, n_gathers=1 << 27, best_of=10, warmup=3):
+    """Random 64-byte block-read rate over a buffer (best of best_of launches,
+    CUDA events on the launching stream).  4 GiB: far larger than L2, the HBM
+    random-block rate; 64 MiB: held by L2, the L2 random-sector rate."""
+    buf = torch.empty(buf_bytes, dtype=torch.uint8, device=dev)
     sink = torch.zeros(1, dtype=torch.int32, device=dev)
     ms = []
     with torch.cuda.stream(stream):
@@ -303,7 +305,7 @@ def gather_probe_phase(aln, torch, dev, stream, buf_gib=4, n_gathers=1 << 27, be
                 ms.append(e0.elapsed_time(e1))
     del buf
     best = min(ms)
-    return {"gbs": n_gathers * 64 / (best / 1000) / 1e9, "unit": "GB/s", "buffer_bytes": buf_gib << 30,
+    return {"gbs": n_gathers * 64 / (best / 1000) / 1e9, "unit": "GB/s", "buffer_bytes": buf_bytes,
             "gathers_per_launch": n_gathers, "bytes_per_gather": 64, "best_of": best_of, "ms": best}
 
 
@@ -343,6 +345,33 @@ def accuracy_report(w, outp, pos, npos, hit_cap, valid):
     return out
 
 
+def roofline(lookups_per_read, n, ms, probes, index_bytes, workload_name):
+    """Achieved algorithmic bytes/s of the search (64 B per Occ lookup of the
+    oracle's canonical count, the D scans included) against the random 64-byte
+    gather rate of the memory that serves the index: L2 when the searched index
+    (Occ blocks + prefix-trie tables of both texts) fits in L2, else HBM; the
+    fraction of the streaming copy peak is reported beside it."""
+    copy_peak, src = _peaks()
+    bytes_per_read = lookups_per_read * BYTES_PER_LOOKUP
+    achieved = bytes_per_read * n / (ms / 1000) / 1e9
+    in_l2 = index_bytes <= L2_BYTES
+    bound = "l2" if in_l2 else "hbm"
+    probe = probes.get(bound)
+    peak = probe["gbs"] if probe else copy_peak
+    traffic = None
+    cap = TRAFFIC_CAPTURE.get(workload_name)
+    if cap and _src_hash() == cap["src_sha256_16"]:
+        traffic = cap["dram_bytes_per_read"] * n
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_source": (f"aln_gather_probe, random 64-byte reads over a {probe['buffer_bytes'] >> 20} MiB "
+                            f"buffer ({'L2-resident' if in_l2 else 'HBM'}), measured in this run") if probe
+                           else f"streaming copy peak ({src})",
+            "index_bytes": int(index_bytes), "copy_peak": copy_peak, "copy_peak_source": src,
+            "frac_of_copy_peak": achieved / copy_peak, "bytes_per_read": bytes_per_read,
+            "occ_lookups_per_s": lookups_per_read * n / (ms / 1000)}
+
+
 def workload_config(name, w, n_per_step, ws, mode="persistent"):
     """The JSON line's config: the workload by name and sizes, the limits."""
     lim = w.params
@@ -353,6 +382,236 @@ def workload_config(name, w, n_per_step, ws, mode="persistent"):
             "strata": "BEST1", "mode": mode,
             "l2": "flushed (512 MiB write) before every step" if mode == "persistent" else "n/a (CPU)",
             "parallelism": f"replicas{ws}" if ws > 1 else "single"}
+
+
+def time_search(al, d, params, res, hits, stream, flush, steps, warmup, torch, graph=None):
+    """Mean device time (ms, CUDA events on the launching stream) of `steps`
+    searches after `warmup` untimed ones, L2 flushed before each."""
+    ms = []
+    with torch.cuda.stream(stream):
+        for it in range(warmup + steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if graph is not None:
+                graph.replay()
+            else:
+                al.search_device(d, params, res, hits, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= warmup:
+                ms.append(e0.elapsed_time(e1))
+    al.check_status()
+    return float(np.mean(ms)), ms
+
+
+def _host_results(aln, res, hits, n, cap):
+    return (res.cpu().numpy().view(aln.RES_DTYPE)[:n].copy(),
+            hits.cpu().numpy().view(aln.HIT_DTYPE)[:n * cap].reshape(n, cap).copy())
+
+
+def _flag_counts(aln, r):
+    fl = r["flags"]
+    return {"incomplete": int(((fl & aln.FLAG_INCOMPLETE) != 0).sum()),
+            "work_limit": int(((fl & aln.FLAG_WORK_LIMIT) != 0).sum()),
+            "cand_overflow": int(((fl & aln.FLAG_CAND_OVERFLOW) != 0).sum()),
+            "hit_overflow": int(((fl & aln.FLAG_HIT_OVERFLOW) != 0).sum()),
+            "no_hit": int((r["n_hits"] == 0).sum())}
+
+
+HIT_FIELDS = ("k", "l", "aligned_len", "strand", "n_diff", "n_mm", "n_gapo", "n_gape")
+
+
+def compare_fields(rg, hg, ro, ho, rows):
+    """Every result field and every written hit field of GPU vs oracle; returns
+    (equal, description of the first difference or None)."""
+    for f in ("c0", "c1", "n_hits", "d_best", "flags"):
+        bad = np.nonzero(rg[f] != ro[f])[0]
+        if bad.size:
+            i = bad[0]
+            return False, f"read {int(rows[i])}: {f} gpu {int(rg[f][i])} oracle {int(ro[f][i])}"
+    cap = hg.shape[1]
+    valid = np.arange(cap)[None, :] < rg["n_hits"][:, None]
+    for f in HIT_FIELDS:
+        bad = np.argwhere(np.where(valid, hg[f], 0) != np.where(valid, ho[f], 0))
+        if bad.size:
+            i, j = bad[0]
+            return False, f"read {int(rows[i])} hit {int(j)}: {f} gpu {int(hg[f][i, j])} oracle {int(ho[f][i, j])}"
+    return True, None
+
+
+def oracle_check(ox, w, rg, hg, sel, hit_cap, threads):
+    """The oracle on the reads `sel` (every field of every read, bit-exact) and the
+    canonical Occ-lookup count per read."""
+    import oracle
+    sub = w.reads.subset(sel)
+    lim = w.params
+    per_read_z = bool(np.any(sub.z != sub.z[0])) if sub.n else False
+    t0 = time.time()
+    ro, ho, look = ox.align(sub.codes, sub.offsets, sub.lens, sub.z if per_read_z else None, z_default=lim["z"],
+                            max_gapo=lim["max_gapo"], max_gape=lim["max_gape"], seed_len=lim["seed_len"],
+                            seed_z=lim["seed_z"], indel_end_skip=lim["indel_end_skip"], hit_cap=hit_cap,
+                            strata=oracle.BEST1, threads=threads)
+    dt = time.time() - t0
+    ok, first_diff = compare_fields(rg[sel], hg[sel], ro, ho, sel)
+    return {"kind": "oracle", "reads": int(sel.size), "bit_exact": bool(ok), "first_difference": first_diff,
+            "oracle_s": dt, "oracle_threads": threads}, look
+
+
+def human_phase(args, aln, torch, dev, stream, flush):
+    """The 3.1 Gbp human-scale text (45 % repeats, 1 % N runs): the paired-end
+    batch (2 x 100 bp, z=4) and the mixed-length batch (36-250 bp, z by length,
+    autotuned, replayed through a captured CUDA graph), persistent vs plain; the
+    oracle index is built on the host cores while the GPU runs, then checks a
+    seeded 1 % of each batch plus every read with a flag, bit-exact; SA positions
+    of the paired batch; placement vs the simulated origins; serving at
+    lambda = 50 requests/s on the resident index."""
+    import threading
+    import oracle
+    from synth.workloads import human_workloads
+    out = {}
+    n_reads = args.human_reads
+    t0 = time.time()
+    mixed, pairs = human_workloads(args.human_ref or None, n_mixed=n_reads, n_pairs=n_reads // 2)
+    out["gen_s"] = time.time() - t0
+    out["ref_bp"] = int(mixed.text.size)
+    threads = max(1, oracle.default_threads() - 1)  # one core stays with the thread that drives the GPU
+    box = {}
+
+    def build_oracle():
+        t = time.time()
+        try:
+            box["ox"] = oracle.OracleIndex(mixed.text, threads=threads)
+        except MemoryError as e:
+            box["err"] = str(e)
+        box["s"] = time.time() - t
+
+    th = threading.Thread(target=build_oracle, daemon=True)
+    if not args.no_oracle:
+        th.start()
+    torch.cuda.empty_cache()
+    t0 = time.time()
+    hix = aln.Index.build(mixed.text, kmer_k=args.kmer_k, device=dev.index, stream=stream)
+    out["index_build"] = {"where": "gpu (fm_index_build_gpu)", "s": time.time() - t0}
+    dix = hix.to_device(dev.index)
+    info = dix.info()
+    index_bytes = 2 * (info["occ_bytes"] + info["kmer_bytes"])
+    del hix
+    al = aln.Aligner(dix)
+    hit_cap = 32
+    blocks = {}
+    for w, name in ((pairs, "pairs"), (mixed, "mixed")):
+        n = w.reads.n
+        per_read_z = name == "mixed"
+        d = al.upload(w.reads.codes, w.reads.offsets, w.reads.lens, w.reads.z if per_read_z else None)
+        res, hits = al.outputs(n, hit_cap)
+        zkw = {"z": 6} if per_read_z else {}
+        pp = aln.Params.from_limits(w.params, hit_cap=hit_cap, mode=aln.MODE_PERSISTENT, **zkw)
+        pl = aln.Params.from_limits(w.params, hit_cap=hit_cap, mode=aln.MODE_PLAIN, **zkw)
+        b = {"reads_per_step": n, "steps": args.human_steps, "warmup": args.human_warmup}
+        graph = None
+        if per_read_z:  # the mixed batch: autotuned schedule, graph replay
+            ns = min(n, 100_000)
+            dsub = dict(d)
+            dsub["n"] = ns
+            t = time.time()
+            pp, tuned_ms = al.autotune(dsub, pp, res, hits, stream)
+            b["autotune"] = {"blocks_per_sm": pp.blocks_per_sm, "smem_stack": pp.smem_stack,
+                             "sample_reads": ns, "sample_ms": tuned_ms, "s": time.time() - t}
+            with torch.cuda.stream(stream):
+                graph = al.capture(d, pp, res, hits)
+            b["graph_replay"] = True
+        ms_p, _ = time_search(al, d, pp, res, hits, stream, flush, args.human_steps, args.human_warmup, torch, graph)
+        rq, hq = _host_results(aln, res, hits, n, hit_cap)
+        ms_l, _ = time_search(al, d, pl, res, hits, stream, flush, args.human_steps, args.human_warmup, torch)
+        rp, hp = _host_results(aln, res, hits, n, hit_cap)
+        inc = ((rp["flags"] | rq["flags"]) & aln.FLAG_INCOMPLETE) != 0
+        vm = np.arange(hit_cap)[None, :] < rq["n_hits"][:, None]
+        same = bool(np.array_equal(rp[~inc], rq[~inc]) and all(
+            np.array_equal(np.where(vm, hp[f], 0)[~inc], np.where(vm, hq[f], 0)[~inc])
+            for f in ("k", "l", "aligned_len", "strand", "n_diff", "n_mm", "n_gapo", "n_gape")))
+        b["persistent"] = {"value": n / (ms_p / 1000), "ms_per_step": ms_p}
+        b["plain"] = {"value": n / (ms_l / 1000), "ms_per_step": ms_l,
+                      "bit_identical_to_persistent_on_complete_reads": same}
+        b["persistent_over_plain"] = ms_l / ms_p
+        b["flags"] = _flag_counts(aln, rq)
+        b["gpu_launches_per_step"] = {"persistent": 4, "plain": 1}
+        b["_out"] = (w, rq, hq, ms_p)
+        blocks[name] = b
+        del d, res, hits, graph
+        torch.cuda.empty_cache()
+    # SA positions of every hit of the paired batch
+    w, rq, hq, _ = blocks["pairs"]["_out"]
+    valid = np.arange(hit_cap)[None, :] < rq["n_hits"][:, None]
+    hits_all = hq[valid]
+    dh = torch.from_numpy(hits_all.view(np.uint8).copy()).to(dev)
+    pos = torch.empty(max(1, hits_all.size * 16), dtype=torch.int64, device=dev)
+    npos = torch.empty(max(1, hits_all.size), dtype=torch.int32, device=dev)
+    sa_ms = []
+    with torch.cuda.stream(stream):
+        for it in range(args.human_warmup + args.human_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dix.sa_to_pos(dh, hits_all.size, 16, pos, npos, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= args.human_warmup:
+                sa_ms.append(e0.elapsed_time(e1))
+    np_h = npos.cpu().numpy().view(np.uint32)[:hits_all.size]
+    pos_h = pos.cpu().numpy().view(np.uint64)[:hits_all.size * 16].reshape(-1, 16)
+    n_pos = int(np_h[np_h <= 16].sum())
+    blocks["pairs"]["sa_to_pos"] = {"hits": int(hits_all.size), "positions": n_pos, "ms": float(np.mean(sa_ms)),
+                                    "positions_per_s": n_pos / (np.mean(sa_ms) / 1000)}
+    blocks["pairs"]["accuracy"] = accuracy_report(w, (rq, hq), pos, npos, hit_cap, valid)
+    # serving on the resident index while the oracle index may still be building
+    if args.human_serve_seconds > 0:
+        out["serving"] = serving_phase(aln, dix, mixed, args.human_serve_lambda, args.human_serve_seconds,
+                                       text_note="the 3.1 Gbp text, resident")
+    # oracle parity: a seeded 1 % of each batch plus every read with a flag
+    if not args.no_oracle:
+        th.join()
+        out["oracle_index_s"] = box.get("s")
+        ox = box.get("ox")
+        if ox is None:
+            out["oracle_error"] = box.get("err", "oracle index not built")
+        for name, b in blocks.items():
+            w, rq, hq, ms_p = b["_out"]
+            if ox is None:
+                continue
+            rng = np.random.default_rng(17)
+            n = w.reads.n
+            flagged = np.nonzero(rq["flags"] != 0)[0]
+            sel = np.unique(np.concatenate([rng.choice(n, max(1, n // 100), replace=False), flagged]))
+            par, look = oracle_check(ox, w, rq, hq, sel, hit_cap, oracle.default_threads())
+            par["sample"] = f"seeded 1 % of the {n}-read batch plus every flagged read ({flagged.size})"
+            par["rows_above_2_31"] = int((hq[sel][np.arange(hit_cap)[None, :] < rq[sel]["n_hits"][:, None]]["l"]
+                                          >= 2 ** 31).sum())
+            b["parity"] = par
+            b["roofline"] = roofline(float(look.mean()), n, ms_p, args._probes, index_bytes, "human_" + name)
+            if name == "pairs":
+                sh = hq[sel][np.arange(hit_cap)[None, :] < rq[sel]["n_hits"][:, None]]
+                oh = np.zeros(sh.size, oracle.HIT_DTYPE)
+                for f in ("k", "l", "aligned_len", "strand"):
+                    oh[f] = sh[f]
+                opos, onpos = ox.positions(oh, 16)
+                gpos, gnpos = al.positions(sh, 16)
+                wide = (sh["l"].astype(np.int64) - sh["k"] + 1) > 16
+                okp = bool((gnpos[wide] == aln.POS_TOO_WIDE).all() and np.array_equal(gnpos[~wide], onpos[~wide])
+                           and all(np.array_equal(gpos[i, :gnpos[i]], opos[i, :gnpos[i]])
+                                   for i in np.nonzero(~wide)[0]))
+                par["positions_bit_exact"] = okp
+                par["positions_hits_checked"] = int(sh.size)
+        del ox
+        box.clear()
+    for b in blocks.values():
+        b.pop("_out", None)
+    out.update(blocks)
+    del al, dix
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -552,14 +811,20 @@ def run_gpu(args):
         "schedule": {"blocks_per_sm": params["persistent"].blocks_per_sm or "max",
                      "autotune_ms": tuned_ms, "graph_replay": bool(graph is not None)},
         # per persistent step: D pre-pass, two visit-order kernels, the search
-        # (one launch per step when the step is a graph replay: captured
-        # searches scan D inside the search kernel)
-        "gpu_launches": args.steps * (1 if graph is not None else 4),
+        # (a graph replay runs the same four kernels)
+        "gpu_launches": args.steps * 4,
         "e2e": {"value": e2e_v, "unit": "reads/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
         "build_s": t_build, "gen_s": t_gen,
     }
+    probes = {}
+    if args.gather_probe:
+        probes["hbm"] = gather_probe_phase(aln, torch, dev, stream)
+        probes["l2"] = gather_probe_phase(aln, torch, dev, stream, buf_bytes=64 << 20)
+        line["gather_probe"] = probes
+    info = dix.info()
+    index_bytes = 2 * (info["occ_bytes"] + info["kmer_bytes"])
     use_oracle = rank == 0 and not args.no_oracle and w.text.size <= args.oracle_max_bp
     if use_oracle:
         import oracle
@@ -592,17 +857,7 @@ def run_gpu(args):
         valid = np.arange(hit_cap)[None, :] < rg["n_hits"][:, None]
         for f in ("k", "l", "aligned_len", "strand", "n_diff", "n_mm", "n_gapo", "n_gape"):
             ok = ok and np.array_equal(np.where(valid, hg[f], 0), np.where(valid, ho[f], 0))
-        lookups_per_read = float(look.mean())
-        alg_bytes = lookups_per_read * BYTES_PER_LOOKUP * n
-        peak, src = _peaks()
-        achieved = alg_bytes / (ms_head / 1000) / 1e9
-        traffic = None
-        if args.workload == TRAFFIC_CAPTURE["workload"] and _src_hash() == TRAFFIC_CAPTURE["src_sha256_16"]:
-            traffic = TRAFFIC_CAPTURE["dram_bytes_per_read"] * n
-        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "traffic": traffic, "peak_source": src,
-                            "bytes_per_read": lookups_per_read * BYTES_PER_LOOKUP,
-                            "occ_lookups_per_s": lookups_per_read * n / (ms_head / 1000)}
+        line["roofline"] = roofline(float(look.mean()), n, ms_head, probes, index_bytes, args.workload)
         line["cpu_baseline"] = {"value": cpu_v, "unit": "reads/s", "cores": threads, "kind": "oracle",
                                 "value_1thread": cpu_v1,
                                 "sample": f"{sel.size} seeded reads of the {n}-read batch, "
@@ -633,10 +888,6 @@ def run_gpu(args):
                          "positions_per_s": n_pos / (np.mean(sa_ms) / 1000)}
     if rank == 0:
         line["accuracy"] = accuracy_report(w, out["persistent"], pos, npos, hit_cap, valid)
-    if args.gather_probe:
-        line["gather_probe"] = gather_probe_phase(aln, torch, dev, stream)
-        if "roofline" in line:
-            line["roofline"]["frac_of_gather_probe"] = line["roofline"]["achieved"] / line["gather_probe"]["gbs"]
     if not use_oracle and rank == 0 and not args.no_oracle:
         line["parity"] = property_checks(w, out["persistent"], pos, npos, hit_cap, hits_all.size, valid)
     if use_oracle:
@@ -665,6 +916,14 @@ def run_gpu(args):
     if args.serve_seconds > 0:
         line["serving"] = serving_phase(aln, dix, w, args.serve_lambda, args.serve_seconds)
         line["p99_ms"] = line["serving"]["p99_ms"]
+    if args.human and ws == 1:
+        args._probes = probes
+        del al, dix, res, hits, d
+        torch.cuda.empty_cache()
+        line["human"] = human_phase(args, aln, torch, dev, stream, flush)
+        if "serving" in line["human"]:
+            line["p99_ms"] = line["human"]["serving"]["p99_ms"]
+            line["p99_source"] = "human.serving (3.1 Gbp text, lambda = %g req/s)" % args.human_serve_lambda
     line["wall_s"] = time.time() - t_all
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -696,6 +955,14 @@ def main():
     ap.add_argument("--reads", type=int, default=0, help="use only the first N reads (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-lambda", type=float, default=100.0)
+    ap.add_argument("--human", type=int, default=1,
+                    help="1: also run the 3.1 Gbp paired and mixed-length batches, oracle-checked, and serving on it")
+    ap.add_argument("--human-ref", type=int, default=0, help="human-scale text length (default 3.1 Gbp)")
+    ap.add_argument("--human-reads", type=int, default=1_000_000, help="reads per human-scale batch")
+    ap.add_argument("--human-steps", type=int, default=3)
+    ap.add_argument("--human-warmup", type=int, default=3)
+    ap.add_argument("--human-serve-seconds", type=float, default=60.0)
+    ap.add_argument("--human-serve-lambda", type=float, default=50.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -68,7 +68,14 @@ extern "C" {
 #define ALN_FLAG_READ_TOO_LONG 0x08  /* len > ALN_MAX_READ_LEN: not searched */
 #define ALN_FLAG_BAD_LIMIT 0x10      /* per-read z > ALN_MAX_Z: not searched */
 #define ALN_FLAG_WORK_LIMIT 0x20     /* per-read expansion limit reached: incomplete */
-#define ALN_FLAG_INCOMPLETE (ALN_FLAG_STACK_OVERFLOW | ALN_FLAG_CAND_OVERFLOW | ALN_FLAG_WORK_LIMIT)
+#define ALN_FLAG_LOOP_LIMIT 0x40     /* the persistent launch reached its loop bound before
+                                        this read was finished: no hits, incomplete */
+#define ALN_FLAG_INCOMPLETE (ALN_FLAG_STACK_OVERFLOW | ALN_FLAG_CAND_OVERFLOW | ALN_FLAG_WORK_LIMIT | \
+                             ALN_FLAG_LOOP_LIMIT)
+
+/* ---------------------------------------------------------------- per-call status bits
+ * written by the kernels into aln_result.status (see aln_search) */
+#define ALN_STATUS_LOOP_LIMIT 0x1u   /* a warp of the persistent launch reached params.loop_limit */
 
 /* ---------------------------------------------------------------- modes */
 #define ALN_MODE_PLAIN 0      /* one launch per batch, one thread per read */
@@ -107,6 +114,18 @@ typedef struct {
 int fm_index_build(const uint8_t *text, uint64_t n, const fm_build_opts *opts, fm_index **out);
 void fm_index_free(fm_index *idx);
 int fm_index_info(const fm_index *idx, fm_index_info_t *info);
+
+/* The same index built on a GPU (Sec. 2: offline encoding; here the encoding of a
+ * human-scale reference takes seconds instead of minutes).  Arguments, defaults
+ * and errors are those of fm_index_build, and the result is the same host index,
+ * byte for byte (the suffix array is unique; everything else is a function of
+ * it).  device: CUDA ordinal that does the work; stream: the work is enqueued on
+ * it and finished before return.  The call allocates about 45 * (n + 1) bytes of
+ * device memory for its duration (suffix array by prefix doubling with radix
+ * sorts of (u64, u32) pairs) and frees it before return; ALN_ENOMEM if that does
+ * not fit, ALN_EDEVICE on a CUDA failure. */
+int fm_index_build_gpu(const uint8_t *text, uint64_t n, const fm_build_opts *opts, int device, void *stream,
+                       fm_index **out);
 
 /* Write / read the index image (little-endian binary, magic "ALNFMIX4").
  * Load returns ALN_EIO on a missing, short or malformed file. */
@@ -156,9 +175,24 @@ typedef struct {
     uint8_t blocks_per_sm;  /* persistent form: resident 128-thread blocks per SM; 0 = as
                                many as fit.  Fewer lanes give each lane more reads, which
                                shortens the tail where a warp waits for its slowest read */
-    uint8_t reserved[2];
+    uint8_t smem_stack;     /* persistent form: search-stack entries per lane held in shared
+                               memory (the rest in local memory): 0 = 8, else one of
+                               ALN_SMEM_STACK_CHOICES; result-neutral */
+    uint8_t reserved0;
     uint32_t work_limit;    /* node expansions per read before ALN_FLAG_WORK_LIMIT; 0 = 2^24 */
+    uint32_t loop_limit;    /* persistent form: trips of the kernel's loop per warp before the
+                               warp stops (ALN_STATUS_LOOP_LIMIT, unfinished reads flagged
+                               ALN_FLAG_LOOP_LIMIT); 0 = 64 * n_reads * (576 + work_limit),
+                               saturating at 2^62: a guard against a livelock, far above the
+                               trips of any batch measured (a trip is one fetch per lane) */
+    uint32_t help_after;    /* persistent form: once the lane searching a read has made this
+                               many node expansions, lanes of its warp that finish their own
+                               reads take its pending subtrees before they take new reads
+                               (the lanes a heavy read gets); 0 = 4096, 0xFFFFFFFF = only
+                               once the read queue is empty; result-neutral */
 } aln_params;
+
+#define ALN_SMEM_STACK_CHOICES {4, 8, 12}
 
 /* One hit, 16 bytes.  The witness (n_diff .. aligned_len) is the minimal one,
  * ordered by (n_diff, n_gapo, n_gape, n_mm, aligned_len), over every valid
@@ -185,6 +219,14 @@ typedef struct {
 typedef struct {
     aln_read_result *reads; /* device, n_reads entries */
     aln_hit *hits;          /* device, n_reads * hit_cap entries; read r at r * hit_cap */
+    uint32_t *status;       /* device, 1 word, may be NULL: cleared by the call on its stream,
+                               then ORed with ALN_STATUS_* bits by the kernels; read it after
+                               the stream has passed the call */
+    void *scratch;          /* device, may be NULL: scratch for the persistent form's D
+                               pre-pass and visit order, aln_search_scratch_bytes(n_reads)
+                               bytes, 256-byte aligned, owned by the call (and by every replay
+                               of a graph that captured it) until it completes */
+    uint64_t scratch_bytes; /* size of scratch */
 } aln_result;
 
 /* Search every read on both strands (Sec. 2: pointer-pair lookup with
@@ -200,28 +242,52 @@ typedef struct {
  * (strand, k, l) merge.  BEST1 keeps hits with diffs <= min(z, d_best + 1).
  * All arrays are device memory, written asynchronously on stream; the caller
  * synchronises.  Returns ALN_EINVAL for bad params, ALN_EDEVICE on a launch
- * failure, ALN_ELIMIT if the persistent queue did not drain within its bound.
- * Per-read problems are reported in flags, never by the status.
+ * failure, ALN_ELIMIT if the index has no reserved queue counter left for a
+ * captured search (see below).  Per-read problems are reported in flags, never
+ * by the return value.  The persistent loop is bounded (params.loop_limit): a
+ * warp that reaches the bound sets ALN_STATUS_LOOP_LIMIT in *out->status, flags
+ * its unfinished reads ALN_FLAG_LOOP_LIMIT and flags every read it then takes
+ * from the queue the same way without searching it, so every read gets a
+ * result; the binding turns the status bit into ALN_ELIMIT.
  * Persistent mode first computes every read's D array in a pre-pass and visits
- * reads in decreasing order of their lower bound; its scratch (256 + 20 bytes
- * per read) comes from a memory pool owned by the device index, allocated and
- * freed in stream order by each call.  While stream is being captured into a
- * graph (or if the pool cannot serve) the search scans D itself and visits
- * reads in input order.  The results are the same either way. */
+ * reads in decreasing order of their lower bound.  Its scratch is out->scratch
+ * if given, else a block from a memory pool owned by the device index,
+ * allocated and freed in stream order by the call.  While stream is being
+ * captured into a graph without out->scratch (or if the pool cannot serve) the
+ * search scans D itself and visits reads in input order.  The results are the
+ * same either way.
+ * Work-queue counters: an uncaptured persistent call takes one of 1024 counters
+ * of the index in turn, so at most 1024 persistent calls on one index may be in
+ * flight at once.  A call made while stream is being captured takes a counter
+ * reserved for that graph for the life of the index (1024 such counters;
+ * ALN_ELIMIT when they are used up); replays of one graph must not overlap each
+ * other, and never share a counter with uncaptured calls. */
 int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
                const aln_params *params, aln_result *out, void *stream);
 
-/* Autotuner for the persistent form: times aln_search of a sample batch (device
- * memory, laid out as for aln_search; scratch receives its results) once for
- * every resident-blocks-per-SM value from 1 to what fits, after one warm-up
- * run, and writes the fastest into params->blocks_per_sm (its time in *best_ms,
- * may be NULL).  The remaining fields of params are used as given.  Blocks on
- * stream.  ALN_EINVAL for an empty sample. */
+/* Bytes of aln_result.scratch the persistent form uses for n_reads reads
+ * (256 + 20 * n_reads).  Host only; never fails. */
+uint64_t aln_search_scratch_bytes(uint32_t n_reads);
+
+/* Autotuner for the persistent form (the scheduler's knobs: how many lanes are
+ * resident, how deep each lane's shared-memory stack is, how soon a heavy read
+ * gets more lanes).  Times aln_search of a sample batch (device memory, laid out
+ * as for aln_search; scratch receives its results): every resident-blocks-per-SM
+ * value from 1 to what fits for every shared-memory stack depth of
+ * ALN_SMEM_STACK_CHOICES (one warm-up run per depth), then help_after in
+ * {1024, 4096, 16384, 0xFFFFFFFF} at the best of those; writes the fastest
+ * blocks_per_sm, smem_stack and help_after into params (its time in *best_ms,
+ * may be NULL).  The remaining fields of params are used as given.  The choice
+ * is cached per (index, sample size, sample z array, limits): a repeated call
+ * returns it without timing.  Blocks on stream.  ALN_EINVAL for an empty
+ * sample. */
 int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint32_t n_reads, aln_params *params,
                  aln_result *scratch, void *stream, float *best_ms);
 
 #define ALN_POS_TOO_WIDE 0xFFFFFFFFu /* n_pos_out value: hit wider than max_width */
 #define ALN_POS_WALK_LIMIT 0xFFFFFFFEu /* n_pos_out value: an LF walk exceeded its bound */
+#define ALN_POS_BAD_HIT 0xFFFFFFFDu  /* n_pos_out value: not a hit of this index (l < k,
+                                        l > n or strand > 1); nothing of the index is read */
 
 /* Reference positions of hits (Sec. 2/3: the pairing stage needs positions
  * from the index).  For hit i of width <= max_width, n_pos_out[i] = width and
@@ -230,8 +296,10 @@ int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint32_t n_reads
  * SA_X[j], for rows j = k..l.  Each SA value comes from the sampled SA after
  * an LF walk to the nearest sampled row (expected sa_sample steps, bounded by
  * 64 * sa_sample; a hit with a walk past the bound gets ALN_POS_WALK_LIMIT).
- * Wider hits get ALN_POS_TOO_WIDE.  hits, pos_out and n_pos_out are device
- * memory; max_width 1..64.  Asynchronous on stream. */
+ * Wider hits get ALN_POS_TOO_WIDE.  A record that cannot be a hit of this index
+ * (l < k, l > n or strand > 1; an unused result slot, say) gets
+ * ALN_POS_BAD_HIT and is checked before any index access.  hits, pos_out and
+ * n_pos_out are device memory; max_width 1..64.  Asynchronous on stream. */
 int sa_to_pos(const fm_dindex *idx, const aln_hit *hits, uint32_t n_hits, uint32_t max_width,
               uint64_t *pos_out, uint32_t *n_pos_out, void *stream);
 
@@ -294,7 +362,8 @@ void aln_server_destroy(aln_server *s);
  * device or fail under memory pressure.
  *
  * aln_search_noalloc runs the persistent search (params.mode is ignored) exactly
- * as aln_search does and writes the same results into the caller's buffers.
+ * as aln_search does and writes the same results into the caller's buffers
+ * (out->scratch is not used: the search scans D in its own loop).
  * Its only scratch, the device work-queue counter, lives in a fixed array of
  * ALN_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that loads
  * the library holds until the process exits.  The call allocates nothing.

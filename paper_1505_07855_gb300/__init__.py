@@ -21,13 +21,15 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401
-    ALN_OK, AlnError, CAND_CAP, FLAG_BAD_LIMIT, FLAG_CAND_OVERFLOW, FLAG_HIT_OVERFLOW,
-    FLAG_INCOMPLETE, FLAG_READ_TOO_LONG, FLAG_STACK_OVERFLOW, FLAG_WORK_LIMIT, HIT_DTYPE,
-    MAX_HIT_CAP, MAX_READ_LEN, MAX_Z, MODE_PERSISTENT, MODE_PLAIN, POS_TOO_WIDE, POS_WALK_LIMIT,
-    RES_DTYPE, STRATA_BEST1, STRATA_FULL, check, lib, library_path,
+    ALN_ELIMIT, ALN_OK, AlnError, CAND_CAP, FLAG_BAD_LIMIT, FLAG_CAND_OVERFLOW, FLAG_HIT_OVERFLOW,
+    FLAG_INCOMPLETE, FLAG_LOOP_LIMIT, FLAG_READ_TOO_LONG, FLAG_STACK_OVERFLOW, FLAG_WORK_LIMIT,
+    HIT_DTYPE, MAX_HIT_CAP, MAX_READ_LEN, MAX_Z, MODE_PERSISTENT, MODE_PLAIN, POS_BAD_HIT,
+    POS_TOO_WIDE, POS_WALK_LIMIT, RES_DTYPE, SMEM_STACK_CHOICES, STATUS_LOOP_LIMIT, STRATA_BEST1,
+    STRATA_FULL, check, lib, library_path,
 )
 
-__all__ = ["Index", "DeviceIndex", "Params", "Aligner", "pack_reads", "gather_probe", "HIT_DTYPE", "RES_DTYPE"]
+__all__ = ["Index", "DeviceIndex", "Params", "Aligner", "pack_reads", "gather_probe", "scratch_bytes",
+           "HIT_DTYPE", "RES_DTYPE"]
 
 
 def _ptr(a) -> int | None:
@@ -47,12 +49,18 @@ class Index:
 
     @classmethod
     def build(cls, text: np.ndarray, n_seed: int = 0, sa_sample: int = 32, kmer_k: int = 0,
-              threads: int = 0) -> "Index":
+              threads: int = 0, device: int | None = None, stream=None) -> "Index":
+        """fm_index_build on the host, or fm_index_build_gpu on CUDA device
+        ``device`` (same index, byte for byte)."""
         t = np.ascontiguousarray(text, dtype=np.uint8)
         opts = _lib.fm_build_opts(n_seed, sa_sample, kmer_k, threads, 0)
         out = ctypes.c_void_p()
-        check(lib().fm_index_build(_ptr(t), t.size, ctypes.byref(opts), ctypes.byref(out)),
-              "fm_index_build")
+        if device is None:
+            check(lib().fm_index_build(_ptr(t), t.size, ctypes.byref(opts), ctypes.byref(out)),
+                  "fm_index_build")
+        else:
+            check(lib().fm_index_build_gpu(_ptr(t), t.size, ctypes.byref(opts), device, _stream_ptr(stream),
+                                           ctypes.byref(out)), "fm_index_build_gpu")
         return cls(out.value)
 
     @classmethod
@@ -109,10 +117,13 @@ class DeviceIndex:
         return _info_dict(i)
 
     def search(self, bases, nmask, offsets, lens, z, n_reads: int, params: "Params",
-               res_out, hits_out, stream=None) -> None:
-        """aln_search on device buffers (torch tensors or raw addresses)."""
+               res_out, hits_out, stream=None, status=None, scratch=None) -> None:
+        """aln_search on device buffers (torch tensors or raw addresses).  status:
+        a device word receiving ALN_STATUS_* bits; scratch: a device buffer of at
+        least scratch_bytes(n_reads) bytes for the persistent form's pre-pass."""
         b = _lib.aln_batch(_ptr(bases), _ptr(nmask), _ptr(offsets), _ptr(lens), _ptr(z))
-        r = _lib.aln_result(_ptr(res_out), _ptr(hits_out))
+        nbytes = 0 if scratch is None else scratch.numel() * scratch.element_size()
+        r = _lib.aln_result(_ptr(res_out), _ptr(hits_out), _ptr(status), _ptr(scratch), nbytes)
         p = params.c()
         check(lib().aln_search(self._h, ctypes.byref(b), n_reads, ctypes.byref(p), ctypes.byref(r),
                                _stream_ptr(stream)), "aln_search")
@@ -126,6 +137,11 @@ class DeviceIndex:
         if h is not None and h.value:
             lib().fm_dindex_free(h)
             self._h = None
+
+
+def scratch_bytes(n_reads: int) -> int:
+    """aln_search_scratch_bytes: bytes of caller scratch the persistent form uses."""
+    return int(lib().aln_search_scratch_bytes(n_reads))
 
 
 def gather_probe(buf, n_gathers: int, seed: int, sink, stream=None) -> None:
@@ -150,11 +166,15 @@ class Params:
     strata: int = STRATA_BEST1
     work_limit: int = 0
     blocks_per_sm: int = 0
+    smem_stack: int = 0
+    loop_limit: int = 0
+    help_after: int = 0
 
     def c(self) -> _lib.aln_params:
         return _lib.aln_params(self.z, self.max_gapo, self.max_gape, self.seed_len, self.seed_z,
                                self.indel_end_skip, self.hit_cap, self.mode, self.strata,
-                               self.blocks_per_sm, (ctypes.c_uint8 * 2)(), self.work_limit)
+                               self.blocks_per_sm, self.smem_stack, 0, self.work_limit,
+                               self.loop_limit, self.help_after)
 
     @classmethod
     def from_limits(cls, lim: dict, **kw) -> "Params":
@@ -189,6 +209,7 @@ class Aligner:
         self.dix = dindex
         self.torch = torch
         self.dev = torch.device("cuda", dindex.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.dev)  # ALN_STATUS_* of the last search
 
     def upload(self, codes, offsets, lens, z=None):
         """Pack reads on the host and copy them to the device."""
@@ -210,46 +231,65 @@ class Aligner:
         hits = t.empty(max(1, n * hit_cap) * HIT_DTYPE.itemsize, dtype=t.uint8, device=self.dev)
         return res, hits
 
-    def search_device(self, d, params: Params, res, hits, stream=None):
+    def search_device(self, d, params: Params, res, hits, stream=None, scratch=None):
         self.dix.search(d["bases"], d["nmask"], d["offsets"], d["lens"], d["z"], d["n"], params,
-                        res, hits, stream)
+                        res, hits, stream, status=self.status, scratch=scratch)
+
+    def last_status(self) -> int:
+        """ALN_STATUS_* bits of the last search (synchronises with the device)."""
+        return int(self.status.item())
+
+    def check_status(self, where: str = "aln_search") -> None:
+        """Raise AlnError(ALN_ELIMIT) if the last search stopped at its loop bound."""
+        st = self.last_status()
+        if st & STATUS_LOOP_LIMIT:
+            raise AlnError(ALN_ELIMIT, where, "the persistent loop reached params.loop_limit; "
+                                              "unfinished reads carry ALN_FLAG_LOOP_LIMIT")
 
     def autotune(self, d, params: Params, res, hits, stream=None) -> tuple:
         """aln_autotune on an uploaded sample: returns (params with the fastest
-        blocks_per_sm, its time in ms)."""
+        blocks_per_sm, smem_stack and help_after, its time in ms)."""
         b = _lib.aln_batch(_ptr(d["bases"]), _ptr(d["nmask"]), _ptr(d["offsets"]), _ptr(d["lens"]), _ptr(d["z"]))
-        r = _lib.aln_result(_ptr(res), _ptr(hits))
+        r = _lib.aln_result(_ptr(res), _ptr(hits), _ptr(self.status), None, 0)
         p = params.c()
         ms = ctypes.c_float()
         check(lib().aln_autotune(self.dix._h, ctypes.byref(b), d["n"], ctypes.byref(p), ctypes.byref(r),
                                  _stream_ptr(stream), ctypes.byref(ms)), "aln_autotune")
-        return dataclasses.replace(params, blocks_per_sm=p.blocks_per_sm), ms.value
+        return dataclasses.replace(params, blocks_per_sm=p.blocks_per_sm, smem_stack=p.smem_stack,
+                                   help_after=p.help_after), ms.value
 
     def capture(self, d, params: Params, res, hits):
         """Capture one search of the uploaded batch d into a CUDA graph; replay it
         with graph.replay() for every new batch copied into the same buffers.
-        One replay at a time (the graph's queue counter is fixed).  A captured
-        persistent search scans D inside the search kernel and visits reads in
-        input order (no per-call scratch); its results are those of aln_search."""
+        The graph owns a queue counter of its own and a scratch buffer (kept on
+        the graph object as ``aln_scratch``) for the D pre-pass and visit order,
+        so a replay runs the same four kernels as aln_search.  Replays of one
+        graph must not overlap each other."""
         t = self.torch
+        scratch = t.empty(scratch_bytes(d["n"]), dtype=t.uint8, device=self.dev)
         side = t.cuda.Stream(device=self.dev)
         side.wait_stream(t.cuda.current_stream(self.dev))
         with t.cuda.stream(side):  # warm-up outside the capture
-            self.search_device(d, params, res, hits, side)
+            self.search_device(d, params, res, hits, side, scratch=scratch)
         t.cuda.current_stream(self.dev).wait_stream(side)
         t.cuda.synchronize(self.dev)
         g = t.cuda.CUDAGraph()
         with t.cuda.graph(g):
-            self.search_device(d, params, res, hits, t.cuda.current_stream(self.dev))
+            self.search_device(d, params, res, hits, t.cuda.current_stream(self.dev), scratch=scratch)
+        g.aln_scratch = scratch
         return g
 
-    def align(self, codes, offsets, lens, params: Params, z=None, stream=None):
-        """Host arrays in, numpy (res[n], hits[n, hit_cap]) out."""
+    def align(self, codes, offsets, lens, params: Params, z=None, stream=None, check_status: bool = True):
+        """Host arrays in, numpy (res[n], hits[n, hit_cap]) out.  Raises
+        AlnError(ALN_ELIMIT) if the search stopped at its loop bound (unless
+        check_status is False: the flagged results are returned)."""
         d = self.upload(codes, offsets, lens, z)
         n = d["n"]
         res, hits = self.outputs(n, params.hit_cap)
         self.search_device(d, params, res, hits, stream)
         self.torch.cuda.synchronize(self.dev)
+        if check_status:
+            self.check_status()
         r = res.cpu().numpy().view(RES_DTYPE)[:n]
         h = hits.cpu().numpy().view(HIT_DTYPE)[:n * params.hit_cap].reshape(n, params.hit_cap)
         return r, h

@@ -25,11 +25,16 @@ FLAG_CAND_OVERFLOW = 0x04
 FLAG_READ_TOO_LONG = 0x08
 FLAG_BAD_LIMIT = 0x10
 FLAG_WORK_LIMIT = 0x20
-FLAG_INCOMPLETE = FLAG_STACK_OVERFLOW | FLAG_CAND_OVERFLOW | FLAG_WORK_LIMIT
+FLAG_LOOP_LIMIT = 0x40
+FLAG_INCOMPLETE = FLAG_STACK_OVERFLOW | FLAG_CAND_OVERFLOW | FLAG_WORK_LIMIT | FLAG_LOOP_LIMIT
+STATUS_LOOP_LIMIT = 0x1
+ALN_ELIMIT = -4
+SMEM_STACK_CHOICES = (4, 8, 12)
 MODE_PLAIN, MODE_PERSISTENT = 0, 1
 STRATA_BEST1, STRATA_FULL = 0, 1
 POS_TOO_WIDE = 0xFFFFFFFF
 POS_WALK_LIMIT = 0xFFFFFFFE
+POS_BAD_HIT = 0xFFFFFFFD
 
 # numpy views of aln_hit (16 B) and aln_read_result (12 B)
 HIT_DTYPE = np.dtype([("k", "<u4"), ("l", "<u4"), ("aligned_len", "<u2"), ("strand", "u1"),
@@ -62,12 +67,14 @@ class aln_params(ctypes.Structure):
                 ("seed_len", ctypes.c_uint8), ("seed_z", ctypes.c_uint8),
                 ("indel_end_skip", ctypes.c_uint8), ("hit_cap", ctypes.c_uint8),
                 ("mode", ctypes.c_uint8), ("strata", ctypes.c_uint8),
-                ("blocks_per_sm", ctypes.c_uint8), ("reserved", ctypes.c_uint8 * 2),
-                ("work_limit", ctypes.c_uint32)]
+                ("blocks_per_sm", ctypes.c_uint8), ("smem_stack", ctypes.c_uint8),
+                ("reserved0", ctypes.c_uint8), ("work_limit", ctypes.c_uint32),
+                ("loop_limit", ctypes.c_uint32), ("help_after", ctypes.c_uint32)]
 
 
 class aln_result(ctypes.Structure):
-    _fields_ = [("reads", ctypes.c_void_p), ("hits", ctypes.c_void_p)]
+    _fields_ = [("reads", ctypes.c_void_p), ("hits", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_uint64)]
 
 
 class aln_server_config(ctypes.Structure):
@@ -84,14 +91,16 @@ class aln_server_stats_t(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("n_slots", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
-assert ctypes.sizeof(aln_params) == 16 and ctypes.sizeof(fm_build_opts) == 24
-assert ctypes.sizeof(fm_index_info_t) == 120
-assert ctypes.sizeof(aln_server_config) == 56 and ctypes.sizeof(aln_server_stats_t) == 72
+assert ctypes.sizeof(aln_params) == 24 and ctypes.sizeof(fm_build_opts) == 24
+assert ctypes.sizeof(fm_index_info_t) == 120 and ctypes.sizeof(aln_result) == 40
+assert ctypes.sizeof(aln_server_config) == 64 and ctypes.sizeof(aln_server_stats_t) == 72
 
 # name -> (restype, argtypes); the exported ABI
 P, u8p = ctypes.c_void_p, ctypes.c_void_p
 SIGNATURES = {
     "fm_index_build": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(fm_build_opts), ctypes.POINTER(P)]),
+    "fm_index_build_gpu": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(fm_build_opts), ctypes.c_int, P,
+                                          ctypes.POINTER(P)]),
     "fm_index_free": (None, [P]),
     "fm_index_info": (ctypes.c_int, [P, ctypes.POINTER(fm_index_info_t)]),
     "fm_index_save": (ctypes.c_int, [P, ctypes.c_char_p]),
@@ -101,6 +110,7 @@ SIGNATURES = {
     "fm_dindex_info": (ctypes.c_int, [P, ctypes.POINTER(fm_index_info_t)]),
     "aln_search": (ctypes.c_int, [P, ctypes.POINTER(aln_batch), ctypes.c_uint32,
                                   ctypes.POINTER(aln_params), ctypes.POINTER(aln_result), P]),
+    "aln_search_scratch_bytes": (ctypes.c_uint64, [ctypes.c_uint32]),
     "sa_to_pos": (ctypes.c_int, [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
     "aln_autotune": (ctypes.c_int, [P, ctypes.POINTER(aln_batch), ctypes.c_uint32, ctypes.POINTER(aln_params),
                                     ctypes.POINTER(aln_result), P, ctypes.POINTER(ctypes.c_float)]),
@@ -143,8 +153,9 @@ def lib(build_if_missing: bool = True):
 
 
 class AlnError(RuntimeError):
-    def __init__(self, status: int, where: str):
-        msg = lib().aln_last_error().decode(errors="replace")
+    def __init__(self, status: int, where: str, msg: str | None = None):
+        if msg is None:
+            msg = lib().aln_last_error().decode(errors="replace")
         super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
         self.status = status
 

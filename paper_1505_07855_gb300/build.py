@@ -17,7 +17,7 @@ LIB = os.path.join(BUILD, "libaln_gb300.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["aln_kernels.cu", "aln_capi.cu"]
+CU_SOURCES = ["aln_kernels.cu", "aln_capi.cu", "index_gpu.cu"]
 CPP_SOURCES = ["index_build.cpp", "aln_server.cpp"]
 HEADERS = ["aln_device.cuh", "aln_search.cuh", "aln_flat.cuh", "aln_internal.h"]
 

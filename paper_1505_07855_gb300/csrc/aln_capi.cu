@@ -5,13 +5,16 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "aln_device.cuh"
 #include "aln_internal.h"
 #include "aln_search.cuh"
 
 namespace aln {
-int persistent_max_blocks(uint32_t z);
+int persistent_max_blocks(uint32_t z, uint32_t smem);
+bool smem_stack_supported(uint32_t smem);
 cudaError_t launch_search(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
                           aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, void *scratch,
                           cudaStream_t st);
@@ -20,17 +23,51 @@ uint64_t search_scratch_bytes(uint32_t n);
 
 using namespace aln;
 
-static constexpr int kQueueSlots = 1024;
+static constexpr int kQueueSlots = 1024;    // counters handed to uncaptured calls in turn
+static constexpr int kCaptureSlots = 1024;  // counters reserved one per captured call
 
 struct fm_dindex {
     int device = 0;
     DIndex X{};
     fm_index_info_t info{};
     void *mem[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-    uint32_t *queues = nullptr;           // persistent-mode queue counters
+    uint32_t *queues = nullptr;           // persistent-mode queue counters: ring, then reserved
     std::atomic<uint32_t> next_queue{0};
+    std::atomic<uint32_t> next_capture{0};
     cudaMemPool_t pool = nullptr;         // stream-ordered per-call scratch (D pre-pass, visit order)
 };
+
+// Search parameters from the ABI struct; ALN_OK or ALN_EINVAL with a message.
+static int search_params(const char *who, const aln_params &P, uint32_t n_reads, SearchParams &sp) {
+    if (P.z > ALN_MAX_Z) return fail(ALN_EINVAL, std::string(who) + ": z > ALN_MAX_Z");
+    if (P.hit_cap < 1) return fail(ALN_EINVAL, std::string(who) + ": hit_cap must be >= 1");
+    if (P.mode > ALN_MODE_PERSISTENT || P.strata > ALN_STRATA_FULL)
+        return fail(ALN_EINVAL, std::string(who) + ": bad mode or strata");
+    if (!smem_stack_supported(P.smem_stack))
+        return fail(ALN_EINVAL, std::string(who) + ": smem_stack must be 0 or one of ALN_SMEM_STACK_CHOICES");
+    sp.z = P.z;
+    sp.max_gapo = P.max_gapo;
+    sp.max_gape = P.max_gape;
+    sp.seed_len = P.seed_len;
+    sp.seed_z = P.seed_z;
+    sp.e = P.indel_end_skip;
+    sp.hit_cap = P.hit_cap;
+    sp.strata = P.strata;
+    sp.work_limit = P.work_limit ? P.work_limit : kDefaultWorkLimit;
+    sp.blocks_per_sm = P.blocks_per_sm;
+    sp.smem_stack = P.smem_stack;
+    sp.help_after = P.help_after ? P.help_after : kDefaultHelpAfter;
+    if (P.loop_limit) {
+        sp.loop_limit = P.loop_limit;
+    } else {  // 64 * n_reads * (576 + work_limit), saturating at 2^62
+        const unsigned long long cap = 1ull << 62, per = 64ull * (576ull + sp.work_limit);
+        sp.loop_limit = (n_reads && per > cap / n_reads) ? cap : per * (n_reads ? n_reads : 1);
+    }
+    sp.status = nullptr;
+    return ALN_OK;
+}
+
+static void tune_forget(const fm_dindex *d);
 
 static int cuda_fail(cudaError_t e, const char *what) {
     return fail(e == cudaErrorMemoryAllocation ? ALN_ENOMEM : ALN_EDEVICE,
@@ -48,6 +85,7 @@ extern "C" void fm_dindex_free(fm_dindex *d) {
     if (d->queues) cudaFree(d->queues);
     if (d->pool) cudaMemPoolDestroy(d->pool);
     cudaSetDevice(prev);
+    tune_forget(d);
     delete d;
 }
 
@@ -90,9 +128,10 @@ extern "C" int fm_index_to_device(const fm_index *idx, int device, void *stream,
         D.n = static_cast<uint32_t>(T.n);
     }
     if (rc == ALN_OK) {
-        if ((e = cudaMalloc(&d->queues, kQueueSlots * sizeof(uint32_t))) != cudaSuccess)
+        const size_t qbytes = (kQueueSlots + kCaptureSlots) * sizeof(uint32_t);
+        if ((e = cudaMalloc(&d->queues, qbytes)) != cudaSuccess)
             rc = cuda_fail(e, "fm_index_to_device: cudaMalloc");
-        else if ((e = cudaMemsetAsync(d->queues, 0, kQueueSlots * sizeof(uint32_t), st)) != cudaSuccess)
+        else if ((e = cudaMemsetAsync(d->queues, 0, qbytes, st)) != cudaSuccess)
             rc = cuda_fail(e, "fm_index_to_device: memset");
     }
     if (rc == ALN_OK) {  // optional: without a pool the search scans D in its own loop
@@ -124,52 +163,67 @@ extern "C" int fm_dindex_info(const fm_dindex *d, fm_index_info_t *info) {
     return ALN_OK;
 }
 
+extern "C" uint64_t aln_search_scratch_bytes(uint32_t n_reads) { return search_scratch_bytes(n_reads); }
+
 extern "C" int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads, const aln_params *params,
                           aln_result *out, void *stream) {
     if (!idx || !batch || !params || !out) return fail(ALN_EINVAL, "aln_search: null argument");
     if (n_reads && (!batch->bases || !batch->offset || !batch->len || !out->reads || !out->hits))
         return fail(ALN_EINVAL, "aln_search: null batch or result array");
     const aln_params &P = *params;
-    if (P.z > ALN_MAX_Z) return fail(ALN_EINVAL, "aln_search: z > ALN_MAX_Z");
-    if (P.hit_cap < 1) return fail(ALN_EINVAL, "aln_search: hit_cap must be >= 1");
-    if (P.mode > ALN_MODE_PERSISTENT || P.strata > ALN_STRATA_FULL) return fail(ALN_EINVAL, "aln_search: bad mode or strata");
     SearchParams sp;
-    sp.z = P.z;
-    sp.max_gapo = P.max_gapo;
-    sp.max_gape = P.max_gape;
-    sp.seed_len = P.seed_len;
-    sp.seed_z = P.seed_z;
-    sp.e = P.indel_end_skip;
-    sp.hit_cap = P.hit_cap;
-    sp.strata = P.strata;
-    sp.work_limit = P.work_limit ? P.work_limit : kDefaultWorkLimit;
-    sp.blocks_per_sm = P.blocks_per_sm;
+    int rc = search_params("aln_search", P, n_reads, sp);
+    if (rc != ALN_OK) return rc;
+    sp.status = out->status;
+    const bool own_scratch = out->scratch && out->scratch_bytes >= search_scratch_bytes(n_reads);
+    if (out->scratch && !own_scratch) return fail(ALN_EINVAL, "aln_search: scratch smaller than aln_search_scratch_bytes");
+    if (own_scratch && reinterpret_cast<uintptr_t>(out->scratch) % 256)
+        return fail(ALN_EINVAL, "aln_search: scratch must be 256-byte aligned");
     ReadBatch rb{batch->bases, batch->nmask, batch->offset, batch->len, batch->z};
     fm_dindex *d = const_cast<fm_dindex *>(idx);
-    uint32_t *queue = d->queues + (d->next_queue.fetch_add(1) % kQueueSlots);
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != idx->device) cudaSetDevice(idx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // Persistent mode takes a per-call scratch from the index's pool, ordered on
-    // the stream (so concurrent calls never share it).  While the stream is being
-    // captured into a graph, or if the pool cannot serve, the search scans D
-    // itself and visits reads in input order: same results.
-    void *scratch = nullptr;
-    if (P.mode == ALN_MODE_PERSISTENT && n_reads && d->pool) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
-        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
-            cudaGetLastError();
-            cs = cudaStreamCaptureStatusActive;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    // Queue counter: uncaptured calls take the ring's next one; a captured call
+    // keeps one of its own for every replay of its graph.
+    uint32_t *queue = nullptr;
+    if (P.mode == ALN_MODE_PERSISTENT && capturing) {
+        const uint32_t c = d->next_capture.fetch_add(1);
+        if (c >= static_cast<uint32_t>(kCaptureSlots)) {
+            if (prev != idx->device) cudaSetDevice(prev);
+            return fail(ALN_ELIMIT, "aln_search: every queue counter reserved for captured searches is in use");
         }
-        if (cs == cudaStreamCaptureStatusNone &&
-            cudaMallocFromPoolAsync(&scratch, search_scratch_bytes(n_reads), d->pool, st) != cudaSuccess) {
-            cudaGetLastError();
-            scratch = nullptr;
+        queue = d->queues + kQueueSlots + c;
+    } else {
+        queue = d->queues + (d->next_queue.fetch_add(1) % kQueueSlots);
+    }
+    // Persistent mode: the D pre-pass and visit order need scratch; the caller's,
+    // else a block of the index's pool ordered on the stream (not while capturing).
+    // Without scratch the search scans D itself and visits reads in input order:
+    // same results.
+    void *scratch = nullptr;
+    bool pooled = false;
+    if (P.mode == ALN_MODE_PERSISTENT && n_reads) {
+        if (own_scratch) {
+            scratch = out->scratch;
+        } else if (d->pool && !capturing) {
+            if (cudaMallocFromPoolAsync(&scratch, search_scratch_bytes(n_reads), d->pool, st) == cudaSuccess) {
+                pooled = true;
+            } else {
+                cudaGetLastError();
+                scratch = nullptr;
+            }
         }
     }
     cudaError_t e = launch_search(idx->X, rb, n_reads, sp, out->reads, out->hits, P.mode, queue, scratch, st);
-    if (scratch) cudaFreeAsync(scratch, st);
+    if (pooled) cudaFreeAsync(scratch, st);
     if (prev != idx->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(e, "aln_search: launch");
     return ALN_OK;
@@ -177,35 +231,107 @@ extern "C" int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t
 
 // ---------------------------------------------------------------- autotuner
 
+namespace {
+// Autotuner choices, cached per (index, sample size, limits).
+struct TuneKey {
+    const fm_dindex *idx;
+    uint32_t n;
+    uint8_t z, gapo, gape, seed_len, seed_z, e, hit_cap, strata;
+    uint32_t work_limit;
+    const void *zarr;
+    bool operator==(const TuneKey &o) const { return std::memcmp(this, &o, sizeof(TuneKey)) == 0; }
+};
+struct TuneVal {
+    uint8_t blocks, smem;
+    uint32_t help_after;
+    float ms;
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+}  // namespace
+
+static void tune_forget(const fm_dindex *d) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::vector<std::pair<TuneKey, TuneVal>> keep;
+    for (auto &kv : g_tune_cache)
+        if (kv.first.idx != d) keep.push_back(kv);
+    g_tune_cache.swap(keep);
+}
+
 extern "C" int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint32_t n_reads, aln_params *params,
                             aln_result *scratch, void *stream, float *best_ms) {
     if (!idx || !sample || !params || !scratch || !n_reads)
         return fail(ALN_EINVAL, "aln_autotune: null argument or empty sample");
+    TuneKey key;
+    std::memset(&key, 0, sizeof key);
+    key.idx = idx;
+    key.n = n_reads;
+    key.z = params->z; key.gapo = params->max_gapo; key.gape = params->max_gape;
+    key.seed_len = params->seed_len; key.seed_z = params->seed_z; key.e = params->indel_end_skip;
+    key.hit_cap = params->hit_cap; key.strata = params->strata;
+    key.work_limit = params->work_limit;
+    key.zarr = sample->z ? static_cast<const void *>(sample->z) : nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto &kv : g_tune_cache)
+            if (kv.first == key) {
+                params->blocks_per_sm = kv.second.blocks;
+                params->smem_stack = kv.second.smem;
+                params->help_after = kv.second.help_after;
+                if (best_ms) *best_ms = kv.second.ms;
+                return ALN_OK;
+            }
+    }
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != idx->device) cudaSetDevice(idx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int maxb = persistent_max_blocks(params->z);
     aln_params p = *params;
     p.mode = ALN_MODE_PERSISTENT;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int rc = ALN_OK, best_b = 0;
+    int rc = ALN_OK, best_b = 0, best_s = 0;
+    uint32_t best_h = params->help_after;
     float best = 0;
-    p.blocks_per_sm = static_cast<uint8_t>(maxb > 0 ? maxb : 1);
-    rc = aln_search(idx, sample, n_reads, &p, scratch, stream);  // warm-up
-    for (int b = 1; b <= maxb && rc == ALN_OK; b++) {
-        p.blocks_per_sm = static_cast<uint8_t>(b);
+    auto timed = [&](float *ms) {
         cudaEventRecord(e0, st);
-        rc = aln_search(idx, sample, n_reads, &p, scratch, stream);
+        int r = aln_search(idx, sample, n_reads, &p, scratch, stream);
         cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ALN_EDEVICE, "aln_autotune: search failed");
+        if (r == ALN_OK && cudaEventSynchronize(e1) != cudaSuccess) r = fail(ALN_EDEVICE, "aln_autotune: search failed");
+        *ms = 0;
+        cudaEventElapsedTime(ms, e0, e1);
+        return r;
+    };
+    // resident blocks per SM x shared-memory stack depth, then the heavy-read help threshold
+    static const int kSmem[] = ALN_SMEM_STACK_CHOICES;
+    for (int smem : kSmem) {
+        const int maxb = persistent_max_blocks(params->z, static_cast<uint32_t>(smem));
+        p.smem_stack = static_cast<uint8_t>(smem);
+        p.blocks_per_sm = static_cast<uint8_t>(maxb > 0 ? maxb : 1);
+        if (rc == ALN_OK) rc = aln_search(idx, sample, n_reads, &p, scratch, stream);  // warm-up
+        for (int b = 1; b <= maxb && rc == ALN_OK; b++) {
+            p.blocks_per_sm = static_cast<uint8_t>(b);
+            float ms = 0;
+            rc = timed(&ms);
+            if (rc == ALN_OK && (best_b == 0 || ms < best)) {
+                best = ms;
+                best_b = b;
+                best_s = smem;
+            }
+        }
+    }
+    static const uint32_t kHelp[] = {1024u, 4096u, 16384u, 0xFFFFFFFFu};
+    p.blocks_per_sm = static_cast<uint8_t>(best_b);
+    p.smem_stack = static_cast<uint8_t>(best_s);
+    for (uint32_t h : kHelp) {
+        if (rc != ALN_OK) break;
+        p.help_after = h;
         float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rc == ALN_OK && (best_b == 0 || ms < best)) {
+        rc = timed(&ms);
+        if (rc == ALN_OK && ms < best) {
             best = ms;
-            best_b = b;
+            best_h = h;
         }
     }
     cudaEventDestroy(e0);
@@ -213,7 +339,11 @@ extern "C" int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint3
     if (prev != idx->device) cudaSetDevice(prev);
     if (rc != ALN_OK) return rc;
     params->blocks_per_sm = static_cast<uint8_t>(best_b);
+    params->smem_stack = static_cast<uint8_t>(best_s);
+    params->help_after = best_h;
     if (best_ms) *best_ms = best;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.push_back({key, TuneVal{static_cast<uint8_t>(best_b), static_cast<uint8_t>(best_s), best_h, best}});
     return ALN_OK;
 }
 
@@ -230,8 +360,9 @@ __global__ void sa_walk_kernel(DIndex X, const aln_hit *hits, uint32_t n_hits, u
     const uint32_t j = static_cast<uint32_t>(tid % max_width);
     if (h >= n_hits) return;
     const aln_hit H = hits[h];
+    if (H.strand > 1 || H.l < H.k || H.l > X.t[0].n) return;  // not a hit of this index
     const uint64_t width = static_cast<uint64_t>(H.l) - H.k + 1;
-    if (H.l < H.k || width > max_width || j >= width) return;
+    if (width > max_width || j >= width) return;
     const DText &T = X.t[H.strand ? 0 : 1];
     const uint32_t mask = (1u << X.sa_shift) - 1u;
     const uint32_t limit = 64u << X.sa_shift;
@@ -261,13 +392,17 @@ __global__ void sa_walk_kernel(DIndex X, const aln_hit *hits, uint32_t n_hits, u
 }
 
 // One thread per hit: width flag and ascending order of its positions.
-__global__ void sa_sort_kernel(const aln_hit *hits, uint32_t n_hits, uint32_t max_width, uint64_t *pos_out,
-                               uint32_t *n_pos_out) {
+__global__ void sa_sort_kernel(const aln_hit *hits, uint32_t n_hits, uint32_t max_width, uint32_t n_text,
+                               uint64_t *pos_out, uint32_t *n_pos_out) {
     const uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= n_hits) return;
     const aln_hit H = hits[h];
+    if (H.strand > 1 || H.l < H.k || H.l > n_text) {
+        n_pos_out[h] = ALN_POS_BAD_HIT;
+        return;
+    }
     const uint64_t width = static_cast<uint64_t>(H.l) - H.k + 1;
-    if (H.l < H.k || width > max_width) {
+    if (width > max_width) {
         n_pos_out[h] = ALN_POS_TOO_WIDE;
         return;
     }
@@ -300,7 +435,8 @@ extern "C" int sa_to_pos(const fm_dindex *idx, const aln_hit *hits, uint32_t n_h
     const uint64_t threads = static_cast<uint64_t>(n_hits) * max_width;
     sa_walk_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(idx->X, hits, n_hits, max_width,
                                                                                  pos_out, n_pos_out);
-    sa_sort_kernel<<<(n_hits + 255) / 256, 256, 0, st>>>(hits, n_hits, max_width, pos_out, n_pos_out);
+    sa_sort_kernel<<<(n_hits + 255) / 256, 256, 0, st>>>(hits, n_hits, max_width, idx->X.t[0].n, pos_out,
+                                                         n_pos_out);
     cudaError_t e = cudaGetLastError();
     if (prev != idx->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(e, "sa_to_pos: launch");
@@ -346,21 +482,12 @@ extern "C" int aln_search_noalloc(const fm_dindex *idx, const aln_batch *batch, 
                                 "work-queue counter in the fixed scratch array)");
     if (n_reads && (!batch->bases || !batch->offset || !batch->len || !out->reads || !out->hits))
         return fail(ALN_EINVAL, "aln_search_noalloc: null batch or result array");
-    const aln_params &P = *params;
-    if (P.z > ALN_MAX_Z) return fail(ALN_EINVAL, "aln_search_noalloc: z > ALN_MAX_Z");
-    if (P.hit_cap < 1) return fail(ALN_EINVAL, "aln_search_noalloc: hit_cap must be >= 1");
-    if (P.strata > ALN_STRATA_FULL) return fail(ALN_EINVAL, "aln_search_noalloc: bad strata");
+    aln_params P = *params;
+    P.mode = ALN_MODE_PERSISTENT;  // the mode field is ignored
     SearchParams sp;
-    sp.z = P.z;
-    sp.max_gapo = P.max_gapo;
-    sp.max_gape = P.max_gape;
-    sp.seed_len = P.seed_len;
-    sp.seed_z = P.seed_z;
-    sp.e = P.indel_end_skip;
-    sp.hit_cap = P.hit_cap;
-    sp.strata = P.strata;
-    sp.work_limit = P.work_limit ? P.work_limit : kDefaultWorkLimit;
-    sp.blocks_per_sm = P.blocks_per_sm;
+    int rc0 = search_params("aln_search_noalloc", P, n_reads, sp);
+    if (rc0 != ALN_OK) return rc0;
+    sp.status = out->status;
     ReadBatch rb{batch->bases, batch->nmask, batch->offset, batch->len, batch->z};
     int prev = 0;
     cudaGetDevice(&prev);

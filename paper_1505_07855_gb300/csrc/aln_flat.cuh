@@ -28,10 +28,7 @@ namespace aln {
 enum : uint32_t { PH_IDLE = 0, PH_DSCAN = 1, PH_DFS = 2, PH_DONE = 3, PH_FREE = 4, PH_WAIT = 5, PH_RETURN = 6 };
 enum : uint32_t { ROLE_OWN = 0, ROLE_HELP = 1 };
 enum : uint32_t { F_NONE = 0, F_OCC = 1, F_TABLE = 2, F_ROOT = 3, F_ZERO = 4 };
-#ifndef ALN_SMEM_STACK
-#define ALN_SMEM_STACK 8
-#endif
-constexpr int kSmemStack = ALN_SMEM_STACK;  // bottom stack entries per lane kept in shared memory
+constexpr int kSmemStackDefault = 8;  // bottom stack entries per lane kept in shared memory
 
 // First entry of level j (strings of length j) in the prefix-trie table.
 __device__ __forceinline__ uint32_t trie_off(uint32_t j) { return ((1u << (2 * j)) - 4u) / 3u; }
@@ -44,10 +41,10 @@ struct FetchReq {
     uint32_t toff;    // F_TABLE: first of the four children entries
 };
 
-template <int STACK_CAP>
+template <int STACK_CAP, int SMEM>
 struct FlatLane {
-    uint4 *sstk;              // entries 0..kSmemStack-1: shared memory, entry j at sstk[j * kThreads]
-    uint4 *stk;               // entries kSmemStack..STACK_CAP-1: local memory
+    uint4 *sstk;              // entries 0..SMEM-1: shared memory, entry j at sstk[j * kThreads]
+    uint4 *stk;               // entries SMEM..STACK_CAP-1: local memory
     uint4 *cand;              // kCandCap candidates (lo, hi, key, -), local memory
     uint4 next;               // the node the next pop would return, kept in registers
     bool has_next;
@@ -65,6 +62,7 @@ struct FlatLane {
     uint32_t outstanding;                // owner: subtrees handed out and not yet returned
     int base;                            // stack bottom (entries below were handed out)
     uint32_t ret_i;                      // helper: next candidate to hand back
+    bool heavy_seen;                     // the last hand-over saw a heavy read with work to give
     ReadView rv;                         // bases of the read being searched
     ReadView own_rv;                     // this lane's shared-memory read columns
 #ifdef ALN_STATS
@@ -182,11 +180,11 @@ struct FlatLane {
     }
 
     __device__ __forceinline__ uint4 stk_get(int j) const {
-        return j < kSmemStack ? sstk[j * kThreads] : stk[j - kSmemStack];
+        return j < SMEM ? sstk[j * kThreads] : stk[j - SMEM];
     }
     __device__ __forceinline__ void stk_set(int j, const uint4 &e) {
-        if (j < kSmemStack) sstk[j * kThreads] = e;
-        else stk[j - kSmemStack] = e;
+        if (j < SMEM) sstk[j * kThreads] = e;
+        else stk[j - SMEM] = e;
     }
 
     __device__ __forceinline__ void push_mem(const uint4 &e) {
@@ -291,6 +289,7 @@ struct FlatLane {
             st_rounds++;
 #endif
             if (phase == PH_IDLE) {
+                if (heavy_seen) return;  // stay idle this trip: the hand-over may give it a heavy read's subtree
                 r = atomicAdd(queue, 1u);
                 if (r >= n_reads) {
                     phase = PH_FREE;
@@ -486,10 +485,50 @@ struct FlatLane {
     }
 
     // Warp-synchronous hand-over, once per trip, all 32 lanes: returning helpers
-    // send one candidate (or their completion) to the owner; free lanes take the
-    // bottom stack entry of a lane with at least two pending entries.
+    // send one candidate (or their completion) to the owner; then lanes without
+    // work take the bottom stack entry of a lane with at least two pending
+    // entries: a free lane (the read queue is empty) from any such lane, an idle
+    // lane (it has finished its read and the queue may still hold reads) only
+    // from a heavy one, a lane searching a read with more than help_after
+    // expansions or a helper, so that a heavy read is searched by the idle lanes
+    // of its warp before they take new reads.  A helper that has handed its
+    // candidates back goes idle (it takes the next read, or becomes free).
+    __device__ __forceinline__ void give(uint32_t lane, uint32_t rcv, uint32_t dnr, const uint32_t *sbase,
+                                         const uint32_t *snbase, uint32_t warp_col) {
+        const unsigned FULL = 0xFFFFFFFFu;
+        const bool giver = lane == dnr;
+        const uint4 e = giver ? stk_get(base) : make_uint4(0, 0, 0, 0);
+        const uint32_t ex = __shfl_sync(FULL, e.x, dnr), ey = __shfl_sync(FULL, e.y, dnr);
+        const uint32_t ez = __shfl_sync(FULL, e.z, dnr), ew = __shfl_sync(FULL, e.w, dnr);
+        const uint32_t o = __shfl_sync(FULL, role == ROLE_OWN ? lane : owner, dnr);
+        const uint32_t hm = __shfl_sync(FULL, m, dnr), hB = __shfl_sync(FULL, B, dnr);
+        const uint32_t hs = __shfl_sync(FULL, s, dnr), hz = __shfl_sync(FULL, z, dnr);
+        const uint32_t h0 = __shfl_sync(FULL, s ? bpb0 : bpa0, dnr);
+        const uint32_t h1 = __shfl_sync(FULL, s ? bpb1 : bpa1, dnr);
+        if (giver) base++;
+        if (lane == o) outstanding++;
+        if (lane == rcv) {
+            role = ROLE_HELP;
+            owner = o;
+            m = hm;
+            B = hB;
+            s = hs;
+            z = hz;
+            if (hs) { bpb0 = h0; bpb1 = h1; } else { bpa0 = h0; bpa1 = h1; }
+            next = make_uint4(ex, ey, ez, ew);
+            has_next = true;
+            sp = 0;
+            base = 0;
+            nc = 0;
+            work = 0;
+            flags = 0;
+            phase = PH_DFS;
+            rv = ReadView{sbase + warp_col + o, snbase + warp_col + o};
+        }
+    }
+
     __device__ __forceinline__ void exchange(uint32_t lane, const uint32_t *sbase, const uint32_t *snbase,
-                                             uint32_t warp_col) {
+                                             uint32_t warp_col, uint32_t help_after) {
         const unsigned FULL = 0xFFFFFFFFu;
         unsigned ret = __ballot_sync(FULL, phase == PH_RETURN);
         while (ret) {
@@ -512,48 +551,57 @@ struct FlatLane {
             if (mine) {
                 if (has) ret_i++;
                 else {
-                    phase = PH_FREE;
+                    phase = PH_IDLE;
                     role = ROLE_OWN;
                     rv = own_rv;
                 }
             }
         }
+        const bool can_give = phase == PH_DFS && (sp - base >= 2 || (sp - base >= 1 && has_next));
+        unsigned donm = __ballot_sync(FULL, can_give);
+        unsigned heavym = __ballot_sync(FULL, can_give && (role == ROLE_HELP || work > help_after));
         unsigned freem = __ballot_sync(FULL, phase == PH_FREE);
-        unsigned donm = __ballot_sync(FULL, phase == PH_DFS && (sp - base >= 2 || (sp - base >= 1 && has_next)));
+        unsigned idlem = __ballot_sync(FULL, phase == PH_IDLE && heavy_seen);
+        heavy_seen = heavym != 0;
         while (freem && donm) {
             const uint32_t rcv = __ffs(freem) - 1, dnr = __ffs(donm) - 1;
             freem &= freem - 1;
             donm &= donm - 1;
-            const bool give = lane == dnr;
-            const uint4 e = give ? stk_get(base) : make_uint4(0, 0, 0, 0);
-            const uint32_t ex = __shfl_sync(FULL, e.x, dnr), ey = __shfl_sync(FULL, e.y, dnr);
-            const uint32_t ez = __shfl_sync(FULL, e.z, dnr), ew = __shfl_sync(FULL, e.w, dnr);
-            const uint32_t o = __shfl_sync(FULL, role == ROLE_OWN ? lane : owner, dnr);
-            const uint32_t hm = __shfl_sync(FULL, m, dnr), hB = __shfl_sync(FULL, B, dnr);
-            const uint32_t hs = __shfl_sync(FULL, s, dnr), hz = __shfl_sync(FULL, z, dnr);
-            const uint32_t h0 = __shfl_sync(FULL, s ? bpb0 : bpa0, dnr);
-            const uint32_t h1 = __shfl_sync(FULL, s ? bpb1 : bpa1, dnr);
-            if (give) base++;
-            if (lane == o) outstanding++;
-            if (lane == rcv) {
-                role = ROLE_HELP;
-                owner = o;
-                m = hm;
-                B = hB;
-                s = hs;
-                z = hz;
-                if (hs) { bpb0 = h0; bpb1 = h1; } else { bpa0 = h0; bpa1 = h1; }
-                next = make_uint4(ex, ey, ez, ew);
-                has_next = true;
-                sp = 0;
-                base = 0;
-                nc = 0;
-                work = 0;
-                flags = 0;
-                phase = PH_DFS;
-                rv = ReadView{sbase + warp_col + o, snbase + warp_col + o};
-            }
+            heavym &= ~(1u << dnr);
+            give(lane, rcv, dnr, sbase, snbase, warp_col);
         }
+        while (idlem && heavym) {
+            const uint32_t rcv = __ffs(idlem) - 1, dnr = __ffs(heavym) - 1;
+            idlem &= idlem - 1;
+            heavym &= heavym - 1;
+            give(lane, rcv, dnr, sbase, snbase, warp_col);
+        }
+    }
+
+    // The launch's loop bound was reached (the warp leaves its loop together):
+    // the lane's own unfinished read, and every read it can still take from the
+    // queue, get an empty result flagged ALN_FLAG_LOOP_LIMIT, so that no read is
+    // left without a result.  A helper's subtree belongs to an owner lane of the
+    // same warp, which is flagged here.
+    __device__ void stop_at_limit(uint32_t lane, uint32_t n_reads, const SearchParams &p, aln_read_result *res,
+                                  uint32_t *queue, const uint32_t *order) {
+        if (lane == 0 && p.status) atomicOr(p.status, ALN_STATUS_LOOP_LIMIT);
+        aln_read_result out;
+        out.c0 = out.c1 = 0;
+        out.n_hits = 0;
+        out.d_best = 255;
+        out.reserved = 0;
+        if (role == ROLE_OWN && (phase == PH_DSCAN || phase == PH_DFS || phase == PH_WAIT)) {
+            out.flags = static_cast<uint8_t>(flags | ALN_FLAG_LOOP_LIMIT);
+            res[r] = out;
+        }
+        out.flags = ALN_FLAG_LOOP_LIMIT;
+        for (;;) {  // ends: the counter only grows, and each lane stops at n_reads
+            uint32_t q = atomicAdd(queue, 1u);
+            if (q >= n_reads) break;
+            res[order ? order[q] : q] = out;
+        }
+        phase = PH_FREE;
     }
 
     __device__ __forceinline__ void apply(const DIndex &X, const uint32_t lo4[4], const uint32_t hi4[4]) {

@@ -52,18 +52,18 @@ __global__ void __launch_bounds__(kThreads) aln_plain_kernel(DIndex X, ReadBatch
 #define ALN_PERSISTENT_MIN_BLOCKS 6  // 6 resident blocks per SM (80 registers, 8 shared stack entries) measured best
 #endif
 
-template <int STACK_CAP>
+template <int STACK_CAP, int SMEM>
 __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persistent_kernel(DIndex X, ReadBatch rb, uint32_t n_reads,
                                                                   SearchParams p, aln_read_result *res,
                                                                   aln_hit *hits, uint32_t *queue,
                                                                   const uint32_t *order, const uint2 *dbp) {
     __shared__ uint32_t s_bases[kReadWords * kThreads];
     __shared__ uint32_t s_nmask[kMaskWords * kThreads];
-    __shared__ uint4 s_stack[kSmemStack * kThreads];
+    __shared__ uint4 s_stack[SMEM * kThreads];
     uint32_t *sb = s_bases + threadIdx.x, *sn = s_nmask + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31u, warp_col = threadIdx.x & ~31u;
-    uint4 stk[STACK_CAP - kSmemStack], cand[kCandCap];
-    FlatLane<STACK_CAP> L;
+    uint4 stk[STACK_CAP - SMEM], cand[kCandCap];
+    FlatLane<STACK_CAP, SMEM> L;
     L.sstk = s_stack + threadIdx.x;
     L.stk = stk;
     L.cand = cand;
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
     L.role = ROLE_OWN;
     L.owner = lane;
     L.outstanding = 0;
+    L.heavy_seen = false;
     L.own_rv = ReadView{sb, sn};
     L.rv = L.own_rv;
 #ifdef ALN_STATS
@@ -84,9 +85,14 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
 #endif
     // All 32 lanes of the warp stay in the loop until every lane is free and the
     // queue is empty; each trip is: control, one converged fetch, the hand-over.
-    // Finite: every read costs at most 2 x 256 D steps and z + 2 passes of at
-    // most work_limit expansions; the guard only caps a bug.
-    for (unsigned long long it = 0; it < (1ull << 44); it++) {
+    // The trip count is warp-uniform; at p.loop_limit trips the warp stops and
+    // flags what it has not finished (stop_at_limit).
+    bool at_limit = false;
+    for (unsigned long long it = 0;; it++) {
+        if (it >= p.loop_limit) {
+            at_limit = true;
+            break;
+        }
         FetchReq fr;
 #ifdef ALN_STATS
         const unsigned long long k0 = clock64();
@@ -125,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
         __syncwarp();
         const unsigned long long k2 = clock64();
 #endif
-        L.exchange(lane, s_bases, s_nmask, warp_col);
+        L.exchange(lane, s_bases, s_nmask, warp_col, p.help_after);
 #ifdef ALN_STATS
         if (lane == 0) {
             st_cc += k1 - k0;
@@ -135,6 +141,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
 #endif
         if (__ballot_sync(0xFFFFFFFFu, L.phase != PH_FREE) == 0) break;
     }
+    if (at_limit) L.stop_at_limit(lane, n_reads, p, res, queue, order);
 #ifdef ALN_STATS
     STAT_ADD(0, st_it); STAT_ADD(1, st_f); STAT_ADD(2, st_occ); STAT_ADD(3, st_tab);
     STAT_ADD(4, st_wi); STAT_ADD(5, st_wl); STAT_ADD(6, L.st_reads); STAT_ADD(7, L.st_rounds);
@@ -225,7 +232,7 @@ __global__ void aln_order_scatter_kernel(const uint2 *dbp, uint32_t n, const uin
 
 int stack_cap_for(uint32_t z) { return z <= 2 ? 19 : (z <= 4 ? 37 : 64); }
 
-template <int CAP>
+template <int CAP, int SMEM>
 static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
                               aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue,
                               void *scratch, cudaStream_t st) {
@@ -236,7 +243,7 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<CAP>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<CAP, SMEM>, kThreads, 0);
         if (p.blocks_per_sm && static_cast<int>(p.blocks_per_sm) < per_sm) per_sm = p.blocks_per_sm;
         if (per_sm < 1) per_sm = 1;
         uint32_t blocks = static_cast<uint32_t>(sms * per_sm);
@@ -256,34 +263,62 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
             aln_order_count_kernel<<<ob, 256, 0, st>>>(dbp, n, counts);
             aln_order_scatter_kernel<<<ob, 256, 0, st>>>(dbp, n, counts, cursor, order);
         }
-        aln_persistent_kernel<CAP><<<blocks, kThreads, 0, st>>>(X, rb, n, p, res, hits, queue, order, dbp);
+        aln_persistent_kernel<CAP, SMEM><<<blocks, kThreads, 0, st>>>(X, rb, n, p, res, hits, queue, order, dbp);
     }
     return cudaGetLastError();
 }
 
-// Resident blocks per SM of the persistent kernel for limit z (occupancy).
-int persistent_max_blocks(uint32_t z) {
+// Resident blocks per SM of the persistent kernel for limit z and a shared-memory
+// stack of smem entries per lane (occupancy).
+template <int SMEM>
+static int max_blocks_smem(uint32_t z) {
     int per_sm = 0;
     switch (stack_cap_for(z)) {
-        case 19: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<19>, kThreads, 0); break;
-        case 37: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<37>, kThreads, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<64>, kThreads, 0); break;
+        case 19: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<19, SMEM>, kThreads, 0); break;
+        case 37: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<37, SMEM>, kThreads, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<64, SMEM>, kThreads, 0); break;
     }
     return per_sm;
 }
+
+int persistent_max_blocks(uint32_t z, uint32_t smem) {
+    switch (smem) {
+        case 4: return max_blocks_smem<4>(z);
+        case 12: return max_blocks_smem<12>(z);
+        default: return max_blocks_smem<8>(z);
+    }
+}
+
+// Shared-memory stack depths the persistent kernel is compiled for.
+bool smem_stack_supported(uint32_t smem) { return smem == 0 || smem == 4 || smem == 8 || smem == 12; }
 
 // Bytes of the optional persistent-mode scratch for n reads: order-sort counters
 // (256 B), D breakpoints (2 x 8 B per read), visit order (4 B per read).
 uint64_t search_scratch_bytes(uint32_t n) { return 256ull + 20ull * n; }
 
+template <int CAP>
+static cudaError_t launch_smem(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
+                               aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, void *scratch,
+                               cudaStream_t st) {
+    switch (p.smem_stack) {
+        case 4: return launch_cap<CAP, 4>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        case 12: return launch_cap<CAP, 12>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        default: return launch_cap<CAP, kSmemStackDefault>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+    }
+}
+
 cudaError_t launch_search(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
                           aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, void *scratch,
                           cudaStream_t st) {
+    if (p.status) {
+        const cudaError_t e = cudaMemsetAsync(p.status, 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) return e;
+    }
     if (n == 0) return cudaSuccess;
     switch (stack_cap_for(p.z)) {
-        case 19: return launch_cap<19>(X, rb, n, p, res, hits, mode, queue, scratch, st);
-        case 37: return launch_cap<37>(X, rb, n, p, res, hits, mode, queue, scratch, st);
-        default: return launch_cap<64>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        case 19: return launch_smem<19>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        case 37: return launch_smem<37>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        default: return launch_smem<64>(X, rb, n, p, res, hits, mode, queue, scratch, st);
     }
 }
 

@@ -34,6 +34,7 @@ constexpr int kReadWords = 16;  // 2-bit words for ALN_MAX_READ_LEN bases
 constexpr int kMaskWords = 8;   // N-mask words
 constexpr int kCandCap = ALN_CAND_CAP;
 constexpr uint32_t kDefaultWorkLimit = 1u << 24;
+constexpr uint32_t kDefaultHelpAfter = 4096;
 
 enum : uint32_t { OP_M = 0, OP_I = 1, OP_D = 2 };
 
@@ -47,6 +48,10 @@ struct ReadBatch {
 
 struct SearchParams {
     uint32_t z, max_gapo, max_gape, seed_len, seed_z, e, hit_cap, strata, work_limit, blocks_per_sm;
+    uint32_t smem_stack;            // persistent form: stack entries per lane in shared memory
+    uint32_t help_after;            // persistent form: expansions after which a read takes idle lanes
+    unsigned long long loop_limit;  // persistent form: loop trips per warp
+    uint32_t *status;               // ALN_STATUS_* bits, or nullptr
 };
 
 // Stack-entry info word: i (8) | n_mm (3) | n_gapo (3) | n_gape (3) | n_ins (3) | seed (3) | last (2)

@@ -478,4 +478,4 @@ extern "C" int aln_pack_reads(const uint8_t *codes, const uint64_t *code_offset,
 
 extern "C" const char *aln_last_error(void) { return aln::g_error.c_str(); }
 
-extern "C" int aln_version(void) { return 101; }  // 1.01: aln_gather_probe, bit-plane index image
+extern "C" int aln_version(void) { return 200; }  // 2.00: loop bound and status word, caller scratch, shared-memory stack choice

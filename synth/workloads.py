@@ -107,6 +107,30 @@ def _human_pairs(ref_len, n_pairs, seed):
                     mates=(m1, m2), meta={"repeats": rep})
 
 
+def human_workloads(ref_len: int | None = None, n_mixed: int = 1_000_000, n_pairs: int = 500_000,
+                    seed: int = 0) -> tuple[Workload, Workload]:
+    """The mixed-length and the paired workload over one shared human-scale text
+    (generated once): the same reads as ``workload("human_mixed", ...)`` and
+    ``workload("human_pairs", ...)`` with these sizes."""
+    ref_len = ref_len or FULL["human_mixed"]["ref_len"]
+    text, nmask, rep = _human_text(ref_len, seed)
+    rng = Rng(seed, "human_mixed")
+    reads = simulate_reads(text, n_mixed, (36, 50, 76, 100, 150, 250), rng.sub("reads"),
+                           sub_rate=(0.01, 0.01), indel_rate=0.0005, indel_lens=(1,),
+                           n_frac=0.02, z_of_len=z_for_length, nmask=nmask)
+    mixed = Workload("human_mixed", text, nmask, reads, dict(LIMITS["human_mixed"]), meta={"repeats": rep})
+    rng = Rng(seed, "human_pairs")
+    m1, m2 = simulate_pairs(text, n_pairs, 100, rng.sub("pairs"), nmask=nmask,
+                            sub_rate=(0.01, 0.01), indel_rate=0.0005, indel_lens=(1,),
+                            n_frac=0.02, z=4)
+    order = np.empty(2 * n_pairs, dtype=np.int64)
+    order[0::2] = np.arange(n_pairs)
+    order[1::2] = n_pairs + np.arange(n_pairs)
+    pairs = Workload("human_pairs", text, nmask, Reads.concat([m1, m2]).subset(order),
+                     dict(LIMITS["human_pairs"]), mates=(m1, m2), meta={"repeats": rep})
+    return mixed, pairs
+
+
 WORKLOADS = {"tiny36": _tiny36, "chr100": _chr100, "human_mixed": _human_mixed,
              "human_pairs": _human_pairs}
 

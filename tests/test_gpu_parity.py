@@ -119,6 +119,46 @@ def test_mixed_lengths_per_read_z(cuda):
     for mode, k in [(aln.MODE_PLAIN, 0), (aln.MODE_PERSISTENT, 0), (aln.MODE_PERSISTENT, 11)]:
         rg, hg = _run(pair, w.reads, lim, hit_cap=32, mode=mode, z=w.reads.z, zmax=6, kmer=k)
         compare(rg, hg, ro, ho, what=f"mixed mode {mode} kmer {k}")
+    # schedule knobs are result-neutral: heavy reads helped at once or only at the
+    # end, every shared-memory stack depth, few resident blocks
+    for help_after, smem, bps in [(1, 4, 0), (0xFFFFFFFF, 12, 0), (64, 8, 1), (0, 12, 2)]:
+        p = aln.Params.from_limits(lim, hit_cap=32, mode=aln.MODE_PERSISTENT, z=6, help_after=help_after,
+                                   smem_stack=smem, blocks_per_sm=bps)
+        rg, hg = pair.als[11].align(w.reads.codes, w.reads.offsets, w.reads.lens, p, z=w.reads.z)
+        compare(rg, hg, ro, ho, what=f"mixed help_after {help_after} smem {smem} blocks {bps}")
+
+
+def _positions_parity(pair, rg, hg, what):
+    """sa_to_pos of every written hit against the oracle's full suffix arrays."""
+    cap = hg.shape[1]
+    hits = hg[np.arange(cap)[None, :] < rg["n_hits"][:, None]]
+    pos, npos = pair.al.positions(hits, 16)
+    ohits = np.zeros(hits.size, oracle.HIT_DTYPE)
+    for f in ("k", "l", "aligned_len", "strand"):
+        ohits[f] = hits[f]
+    opos, onpos = pair.ox.positions(ohits, 16)
+    wide = (hits["l"].astype(np.int64) - hits["k"] + 1) > 16
+    assert (npos[wide] == aln.POS_TOO_WIDE).all(), what
+    assert np.array_equal(npos[~wide], onpos[~wide]), what
+    for i in np.nonzero(~wide)[0]:
+        assert np.array_equal(pos[i, :npos[i]], opos[i, :npos[i]]), f"{what}: hit {i}"
+    return int((~wide).sum())
+
+
+def test_pairs_recipe_parity(cuda):
+    """The paired-end recipe (2 x 100 bp, fragment ~ Normal(500, 50), mates on
+    opposite strands, 0.1 % chimeric pairs, repeats and N runs) at 3 Mbp: both
+    mates of every pair in one batch, every read bit-exact in the plain and the
+    persistent form, and the SA positions of every hit equal to the oracle's."""
+    w = workload("human_pairs", ref_len=3_000_000, n_reads=3000, seed=4)
+    assert w.reads.n == 6000 and (w.reads.true_strand[0::2] != w.reads.true_strand[1::2]).mean() > 0.99
+    pair = Pair(w.text, kmers=[0, BENCH_KMER])
+    ro, ho, _ = oracle_align(pair.ox, w.reads, w.params, 32, oracle.BEST1)
+    for mode, k in [(aln.MODE_PLAIN, 0), (aln.MODE_PERSISTENT, 0), (aln.MODE_PERSISTENT, BENCH_KMER)]:
+        rg, hg = _run(pair, w.reads, w.params, mode=mode, kmer=k)
+        compare(rg, hg, ro, ho, what=f"pairs mode {mode} kmer {k}")
+    assert (rg["n_hits"] > 0).mean() > 0.95
+    assert _positions_parity(pair, rg, hg, "pairs positions") > 5000
 
 
 def test_chr100_scaled_parity(cuda):
@@ -226,11 +266,18 @@ def test_autotune_and_graph_replay(cuda, tiny36):
     d = al.upload(w.reads.codes, w.reads.offsets, w.reads.lens)
     res, hits = al.outputs(d["n"], 16)
     tuned, ms = al.autotune(d, p, res, hits)
-    assert 1 <= tuned.blocks_per_sm <= 16 and ms > 0
+    assert 1 <= tuned.blocks_per_sm <= 16 and ms > 0 and tuned.smem_stack in aln.SMEM_STACK_CHOICES
+    assert tuned.help_after in (1024, 4096, 16384, 0xFFFFFFFF)
+    again, ms2 = al.autotune(d, p, res, hits)  # cached per index, sample and limits
+    assert (again.blocks_per_sm, again.smem_stack, again.help_after, ms2) == \
+        (tuned.blocks_per_sm, tuned.smem_stack, tuned.help_after, ms)
     ref = al.align(w.reads.codes, w.reads.offsets, w.reads.lens, p)
     got = al.align(w.reads.codes, w.reads.offsets, w.reads.lens, tuned)
     assert np.array_equal(ref[0], got[0])
+    ro, ho, _ = oracle_align(pair.ox, w.reads, w.params, 16, oracle.BEST1)
+    compare(got[0], got[1], ro, ho, what="autotuned")
     g = al.capture(d, p, res, hits)
+    assert g.aln_scratch.numel() == aln.scratch_bytes(d["n"])
     for _ in range(2):
         res.fill_(0)
         hits.fill_(0)
@@ -240,4 +287,6 @@ def test_autotune_and_graph_replay(cuda, tiny36):
         g.replay()
         torch.cuda.synchronize()
         r = res.cpu().numpy().view(aln.RES_DTYPE)[:d["n"]]
-        assert np.array_equal(r, ref[0])
+        h = hits.cpu().numpy().view(aln.HIT_DTYPE)[:d["n"] * 16].reshape(d["n"], 16)
+        compare(r, h, ro, ho, what="graph replay")
+        assert al.last_status() == 0
