@@ -24,6 +24,12 @@ RES_DTYPE = np.dtype([("c0", "<u4"), ("c1", "<u4"), ("n_hits", "u1"), ("flags", 
                       ("d_best", "u1"), ("pad", "u1")])
 assert HIT_DTYPE.itemsize == 16 and RES_DTYPE.itemsize == 12
 
+PAIR_DTYPE = np.dtype([("pos", "<u8", (2,)), ("insert", "<u4"), ("n_proper", "<u2"), ("strand", "u1", (2,)),
+                       ("flags", "u1"), ("pad", "u1", (3,)), ("pad2", "<u4")])
+assert PAIR_DTYPE.itemsize == 32
+PAIR_MAPPED1, PAIR_MAPPED2, PAIR_PLACED1, PAIR_PLACED2 = 0x01, 0x02, 0x04, 0x08
+PAIR_UNIQUE, PAIR_PROPER, PAIR_DISCORDANT = 0x10, 0x20, 0x40
+
 FLAG_HIT_OVERFLOW = 0x01
 FLAG_READ_TOO_LONG = 0x08
 FLAG_BAD_LIMIT = 0x10
@@ -71,6 +77,8 @@ def lib():
         L.orc_align.argtypes = [P, P, P, P, P, u64, ctypes.POINTER(_Params), i32, P, P, P]
         L.orc_dscan.restype = i32
         L.orc_dscan.argtypes = [P, i32, P, i32, P]
+        L.orc_pair_resolve.restype = i32
+        L.orc_pair_resolve.argtypes = [P, P, P, ctypes.c_uint32, u64, i32, P, P]
         L.orc_mix64.restype = u64
         L.orc_mix64.argtypes = [u64]
         L.orc_positions.restype = i32
@@ -177,6 +185,22 @@ class OracleIndex:
         if rc != 0:
             raise ValueError("bad oracle parameters")
         return res, hits[:, :hit_cap], look
+
+    def pair_resolve(self, res: np.ndarray, hits: np.ndarray, max_place: int = 16):
+        """Pairing of reads 2p (mate 1) and 2p+1 (mate 2) from their search results
+        (res[n], hits[n, hit_cap], n even).  Returns (pairs PAIR_DTYPE[n / 2],
+        stats dict: n_unique, q1, q2, q3, lo, hi)."""
+        res = np.ascontiguousarray(res, dtype=RES_DTYPE)
+        hits = np.ascontiguousarray(hits, dtype=HIT_DTYPE)
+        n = res.size
+        if n % 2 or hits.shape[0] != n:
+            raise ValueError("pairs need an even number of reads and hits[n, hit_cap]")
+        out = np.zeros(n // 2, PAIR_DTYPE)
+        st = np.zeros(8, np.uint32)
+        if lib().orc_pair_resolve(self._h, _ptr(res), _ptr(hits), hits.shape[1], n // 2, max_place, _ptr(out),
+                                  _ptr(st)) != 0:
+            raise ValueError("bad pairing arguments")
+        return out, dict(zip(("n_unique", "q1", "q2", "q3", "lo", "hi"), (int(x) for x in st[:6])))
 
     def positions(self, hits: np.ndarray, max_width: int = 16):
         """Per hit: sorted forward-strand positions (array of max_width) and count."""

@@ -705,3 +705,190 @@ int orc_positions(const orc_index *ix, const orc_hit *h, uint64_t nh, uint32_t m
     }
     return 0;
 }
+
+/* ------------------------------------------------------------ pairing
+ *
+ * Paired reads after the search (the pipeline's pairing stage, Sec. 2 and the
+ * pipeline of Sec. 3: mate hits are combined using the fragment length).  Read
+ * 2p is mate 1 and read 2p+1 mate 2 of pair p.  The paper gives no rule; the
+ * one restated here (the project's reading, written out in the design notes):
+ *  - placements of a mate: every position of every hit in its best stratum
+ *    (n_diff == d_best), each with the hit's strand, target length and n_diff.
+ *    A mate is placed iff 1 <= c0 <= max_place (c0 = its number of best
+ *    placements) and all of its best hits were written;
+ *  - a combination (one placement of each mate) is FR if the strands differ;
+ *    with f the forward and v the reverse placement, its insert is
+ *    v.pos + v.len - f.pos (may be <= 0);
+ *  - insert-size window: over the pairs whose mates both have c0 == 1 and whose
+ *    single combination is FR with 1 <= insert <= 65535 (the unique pairs), the
+ *    sorted inserts s[0..u-1] give q1 = s[u/4], q2 = s[u/2], q3 = s[3u/4]
+ *    (integer division) and the window [max(1, q1 - 2 (q3 - q1)),
+ *    min(65535, q3 + 2 (q3 - q1))]; with fewer than 8 unique pairs the window is
+ *    [1, 65535] and q1 = q2 = q3 = 0;
+ *  - a combination is proper if FR with its insert inside the window; the pair's
+ *    choice is the proper combination smallest by (n_diff1 + n_diff2,
+ *    |insert - q2|, insert, pos1, pos2, strand1, len1, len2);
+ *  - flags: 1, 2 mate 1 / 2 has a hit; 4, 8 mate 1 / 2 is placed; 16 unique
+ *    pair; 32 proper (a choice exists); 64 discordant (both placed, no proper
+ *    combination).
+ */
+#define OP_MAPPED1 0x01
+#define OP_MAPPED2 0x02
+#define OP_PLACED1 0x04
+#define OP_PLACED2 0x08
+#define OP_UNIQUE 0x10
+#define OP_PROPER 0x20
+#define OP_DISCORDANT 0x40
+#define ISIZE_MAX 65535
+
+typedef struct {
+    uint64_t pos[2];
+    uint32_t insert;
+    uint16_t n_proper;
+    uint8_t strand[2];
+    uint8_t flags;
+    uint8_t pad[3];
+    uint32_t pad2;
+} orc_pair;
+
+typedef struct {
+    uint32_t n_unique, q1, q2, q3, lo, hi, pad[2];
+} orc_pair_stats;
+
+typedef struct { uint64_t pos; uint32_t len; uint8_t strand, n_diff; } placement;
+
+/* Placements of one read (its best stratum), from the full suffix arrays. */
+static int placements_of(const orc_index *ix, const orc_res *r, const orc_hit *h, int max_place, placement *out)
+{
+    if (r->n_hits == 0 || r->c0 < 1 || r->c0 > (uint32_t)max_place) return -1;
+    uint64_t n = ix->t[0].n;
+    int k = 0;
+    for (int j = 0; j < r->n_hits; j++) {
+        if (h[j].n_diff != r->d_best) continue;
+        for (uint64_t row = h[j].k; row <= h[j].l; row++) {
+            if (k == max_place) return -1;
+            out[k].pos = h[j].strand ? ix->t[0].sa[row] : n - ix->t[1].sa[row] - h[j].aligned_len;
+            out[k].len = h[j].aligned_len;
+            out[k].strand = h[j].strand;
+            out[k].n_diff = h[j].n_diff;
+            k++;
+        }
+    }
+    return (uint32_t)k == r->c0 ? k : -1;  /* every best placement was written */
+}
+
+/* Insert of a combination (0 and FR flag clear if the strands are equal). */
+static int64_t insert_of(const placement *a, const placement *b, int *fr)
+{
+    *fr = a->strand != b->strand;
+    if (!*fr) return 0;
+    const placement *f = a->strand == 0 ? a : b, *v = a->strand == 0 ? b : a;
+    return (int64_t)v->pos + (int64_t)v->len - (int64_t)f->pos;
+}
+
+static int u32_cmp(const void *a, const void *b)
+{
+    uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
+    return x < y ? -1 : (x > y);
+}
+
+int orc_pair_resolve(const orc_index *ix, const orc_res *res, const orc_hit *hits, uint32_t hit_cap,
+                     uint64_t n_pairs, int max_place, orc_pair *out, orc_pair_stats *st)
+{
+    if (!ix || max_place < 1 || max_place > 64) return -1;
+    placement *pa = (placement *)malloc(max_place * sizeof(placement));
+    placement *pb = (placement *)malloc(max_place * sizeof(placement));
+    uint32_t *ins = (uint32_t *)malloc((n_pairs ? n_pairs : 1) * sizeof(uint32_t));
+    if (!pa || !pb || !ins) return -1;
+    /* unique pairs -> insert-size window */
+    uint64_t u = 0;
+    for (uint64_t p = 0; p < n_pairs; p++) {
+        const orc_res *r1 = &res[2 * p], *r2 = &res[2 * p + 1];
+        if (r1->c0 != 1 || r2->c0 != 1) continue;
+        int na = placements_of(ix, r1, hits + 2 * p * hit_cap, max_place, pa);
+        int nb = placements_of(ix, r2, hits + (2 * p + 1) * hit_cap, max_place, pb);
+        if (na != 1 || nb != 1) continue;
+        int fr;
+        int64_t x = insert_of(&pa[0], &pb[0], &fr);
+        if (fr && x >= 1 && x <= ISIZE_MAX) ins[u++] = (uint32_t)x;
+    }
+    memset(st, 0, sizeof *st);
+    st->n_unique = (uint32_t)u;
+    st->lo = 1;
+    st->hi = ISIZE_MAX;
+    if (u >= 8) {
+        qsort(ins, u, sizeof(uint32_t), u32_cmp);
+        st->q1 = ins[u / 4];
+        st->q2 = ins[u / 2];
+        st->q3 = ins[(3 * u) / 4];
+        int64_t iqr = (int64_t)st->q3 - st->q1;
+        int64_t lo = (int64_t)st->q1 - 2 * iqr, hi = (int64_t)st->q3 + 2 * iqr;
+        st->lo = (uint32_t)(lo < 1 ? 1 : lo);
+        st->hi = (uint32_t)(hi > ISIZE_MAX ? ISIZE_MAX : hi);
+    }
+    /* each pair: proper combinations and the choice */
+    for (uint64_t p = 0; p < n_pairs; p++) {
+        const orc_res *r1 = &res[2 * p], *r2 = &res[2 * p + 1];
+        orc_pair *o = &out[p];
+        memset(o, 0, sizeof *o);
+        o->pos[0] = o->pos[1] = UINT64_MAX;
+        o->strand[0] = o->strand[1] = 255;
+        if (r1->n_hits) o->flags |= OP_MAPPED1;
+        if (r2->n_hits) o->flags |= OP_MAPPED2;
+        int na = placements_of(ix, r1, hits + 2 * p * hit_cap, max_place, pa);
+        int nb = placements_of(ix, r2, hits + (2 * p + 1) * hit_cap, max_place, pb);
+        if (na > 0) o->flags |= OP_PLACED1;
+        if (nb > 0) o->flags |= OP_PLACED2;
+        if (na <= 0 || nb <= 0) continue;
+        if (na == 1 && nb == 1) {
+            int fr;
+            int64_t x = insert_of(&pa[0], &pb[0], &fr);
+            if (fr && x >= 1 && x <= ISIZE_MAX) o->flags |= OP_UNIQUE;
+        }
+        uint32_t nproper = 0;
+        int best_i = -1, best_j = -1;
+        int64_t best_x = 0;
+        for (int i = 0; i < na; i++) {
+            for (int j = 0; j < nb; j++) {
+                int fr;
+                int64_t x = insert_of(&pa[i], &pb[j], &fr);
+                if (!fr || x < (int64_t)st->lo || x > (int64_t)st->hi) continue;
+                nproper++;
+                int better = best_i < 0;
+                if (!better) {
+                    int d = pa[i].n_diff + pb[j].n_diff, db = pa[best_i].n_diff + pb[best_j].n_diff;
+                    int64_t e = x > st->q2 ? x - st->q2 : st->q2 - x;
+                    int64_t eb = best_x > st->q2 ? best_x - st->q2 : st->q2 - best_x;
+                    if (d != db) better = d < db;
+                    else if (e != eb) better = e < eb;
+                    else if (x != best_x) better = x < best_x;
+                    else if (pa[i].pos != pa[best_i].pos) better = pa[i].pos < pa[best_i].pos;
+                    else if (pb[j].pos != pb[best_j].pos) better = pb[j].pos < pb[best_j].pos;
+                    else if (pa[i].strand != pa[best_i].strand) better = pa[i].strand < pa[best_i].strand;
+                    else if (pa[i].len != pa[best_i].len) better = pa[i].len < pa[best_i].len;
+                    else better = pb[j].len < pb[best_j].len;
+                }
+                if (better) {
+                    best_i = i;
+                    best_j = j;
+                    best_x = x;
+                }
+            }
+        }
+        o->n_proper = (uint16_t)(nproper > 65535 ? 65535 : nproper);
+        if (best_i >= 0) {
+            o->flags |= OP_PROPER;
+            o->pos[0] = pa[best_i].pos;
+            o->pos[1] = pb[best_j].pos;
+            o->strand[0] = pa[best_i].strand;
+            o->strand[1] = pb[best_j].strand;
+            o->insert = (uint32_t)best_x;
+        } else {
+            o->flags |= OP_DISCORDANT;
+        }
+    }
+    free(pa);
+    free(pb);
+    free(ins);
+    return 0;
+}

@@ -9,6 +9,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_pairs as pair_pins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "aln_oracle.c")
@@ -29,6 +30,15 @@ MUTANTS = {
     "bucket_pads_with_t": ("key = 4 * key + (i + j < n ? text[i + j] : 0);", "key = 4 * key + (i + j < n ? text[i + j] : 3);"),
     "bucket_key_drops_symbol": ("for (int j = 0; j < bk; j++) key", "for (int j = 1; j < bk; j++) key"),
     "mix64_shift": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
+    "pair_insert_without_len": ("return (int64_t)v->pos + (int64_t)v->len - (int64_t)f->pos;",
+                                "return (int64_t)v->pos - (int64_t)f->pos;"),
+    "pair_window_3iqr": ("int64_t lo = (int64_t)st->q1 - 2 * iqr, hi = (int64_t)st->q3 + 2 * iqr;",
+                         "int64_t lo = (int64_t)st->q1 - 3 * iqr, hi = (int64_t)st->q3 + 3 * iqr;"),
+    "pair_median_index": ("st->q2 = ins[u / 2];", "st->q2 = ins[(u + 1) / 2];"),
+    "pair_tie_far_from_median": ("else if (e != eb) better = e < eb;", "else if (e != eb) better = e > eb;"),
+    "pair_same_strand_is_fr": ("*fr = a->strand != b->strand;", "*fr = 1;"),
+    "pair_reverse_pos_no_len": ("out[k].pos = h[j].strand ? ix->t[0].sa[row] : n - ix->t[1].sa[row] - h[j].aligned_len;",
+                                "out[k].pos = h[j].strand ? ix->t[0].sa[row] : n - ix->t[1].sa[row];"),
     "dollar_largest": ("return li < lj ? -1 : (li > lj ? 1 : 0);", "return li > lj ? -1 : (li < lj ? 1 : 0);"),
     "best1_no_second_stratum": ("int keep_max = (p->strata == 1) ? z : (d_best + 1 <= z ? d_best + 1 : z);",
                                 "int keep_max = (p->strata == 1) ? z : d_best;"),
@@ -61,6 +71,8 @@ def _pin_calls():
         lambda: pins.test_every_position_every_edit(2),
         lambda: pins.test_against_brute_force(*c[2], "FULL"),
         lambda: pins.test_every_pair_of_edits_in_seed(1),
+        pair_pins.test_pairing_hand_example,
+        pair_pins.test_pairing_recovers_the_generated_fragments,
     ]
 
 
