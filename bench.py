@@ -120,15 +120,34 @@ def _dist():
     return ws, rank, local
 
 
-def replica_index(aln, text, kmer_k, rank, ws, barrier, path):
-    """Replicas: rank 0 builds the index and saves it, the other ranks load the
-    image after the barrier (no collective touches the data path)."""
+def replica_index(aln, text, kmer_k, rank, ws, barrier, path, device=None):
+    """Replicas: rank 0 builds the index (on its GPU when device is given) and
+    saves it, the other ranks load the image after the barrier (no collective
+    touches the data path)."""
     if ws > 1:
         if rank == 0:
-            aln.Index.build(text, kmer_k=kmer_k).save(path)
+            aln.Index.build(text, kmer_k=kmer_k, device=device).save(path)
         barrier()
         return aln.Index.load(path)
-    return aln.Index.build(text, kmer_k=kmer_k)
+    return aln.Index.build(text, kmer_k=kmer_k, device=device)
+
+
+def partition_range(n, rank, ws):
+    """Reads [lo, hi) of rank `rank` out of ws replicas: contiguous ranges of
+    near-equal size in read order (every GPU holds the whole index)."""
+    return n * rank // ws, n * (rank + 1) // ws
+
+
+def concat_over_ranks(parts, ws):
+    """Per-rank result arrays (a tuple of numpy arrays over the rank's reads),
+    concatenated in rank order on every rank: the results of the whole batch in
+    read order.  No collective touches the timed search; this runs after it."""
+    if ws <= 1:
+        return parts
+    import torch.distributed as dist
+    objs = [None] * ws
+    dist.all_gather_object(objs, parts)
+    return tuple(np.concatenate([o[i] for o in objs]) for i in range(len(parts)))
 
 
 def max_over_ranks(values, ws, device=None):
@@ -674,32 +693,38 @@ def run_gpu(args):
     if args.reads and w.reads.n > args.reads:
         w.reads = w.reads.subset(np.arange(args.reads))
     lim = w.params
-    n = w.reads.n
+    n = w.reads.n  # reads of the whole job
     per_read_z = args.workload == "human_mixed"
+    # replicas: every GPU holds the whole index and searches its own range of reads
+    lo, hi = partition_range(n, rank, ws)
+    rl = w.reads.subset(np.arange(lo, hi)) if ws > 1 else w.reads
+    n_local = rl.n
+    build_dev = local if args.index_build == "gpu" else None
     # index: rank 0 builds and saves, the other replicas load the image
     t0 = time.time()
     if ws > 1:
         hix = replica_index(aln, w.text, args.kmer_k, rank, ws, torch.distributed.barrier,
-                            f"/tmp/aln_bench_{args.workload}.fmi")
+                            f"/tmp/aln_bench_{args.workload}.fmi", device=build_dev)
     elif args.index_cache and os.path.exists(args.index_cache):
         hix = aln.Index.load(args.index_cache)
     else:
-        hix = aln.Index.build(w.text, kmer_k=args.kmer_k)
+        hix = aln.Index.build(w.text, kmer_k=args.kmer_k, device=build_dev)
         if args.index_cache:
             hix.save(args.index_cache)
     t_build = time.time() - t0
     dix = hix.to_device(local)
+    del hix
     al = aln.Aligner(dix)
     stream = torch.cuda.Stream(device=dev)
-    bases, nmask, offs = aln.pack_reads(w.reads.codes, w.reads.offsets, w.reads.lens)
-    lens = np.ascontiguousarray(w.reads.lens)
+    bases, nmask, offs = aln.pack_reads(rl.codes, rl.offsets, rl.lens)
+    lens = np.ascontiguousarray(rl.lens)
     d = {"bases": torch.from_numpy(bases.view(np.int32)).to(dev),
          "nmask": torch.from_numpy(nmask.view(np.int32)).to(dev),
          "offsets": torch.from_numpy(offs.view(np.int64)).to(dev),
          "lens": torch.from_numpy(lens.view(np.int16)).to(dev),
-         "z": torch.from_numpy(np.ascontiguousarray(w.reads.z)).to(dev) if per_read_z else None, "n": n}
+         "z": torch.from_numpy(np.ascontiguousarray(rl.z)).to(dev) if per_read_z else None, "n": n_local}
     hit_cap = 32
-    res, hits = al.outputs(n, hit_cap)
+    res, hits = al.outputs(n_local, hit_cap)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     modes = {"persistent": aln.MODE_PERSISTENT, "plain": aln.MODE_PLAIN}
     params = {k: aln.Params.from_limits(lim, hit_cap=hit_cap, mode=m, blocks_per_sm=args.blocks_per_sm,
@@ -708,7 +733,7 @@ def run_gpu(args):
 
     tuned_ms = None
     if args.autotune:
-        ns = min(n, 100_000)
+        ns = min(n_local, 100_000)
         dsub = dict(d)
         dsub["n"] = ns
         params["persistent"], tuned_ms = al.autotune(dsub, params["persistent"], res, hits, stream)
@@ -749,12 +774,15 @@ def run_gpu(args):
             torch.cuda.synchronize(dev)
             ms = [a.elapsed_time(b) for a, b in evs]
             times[mode] = ms
-            out[mode] = (res.cpu().numpy().view(aln.RES_DTYPE)[:n].copy(),
-                         hits.cpu().numpy().view(aln.HIT_DTYPE)[:n * hit_cap].reshape(n, hit_cap).copy())
+            out[mode] = (res.cpu().numpy().view(aln.RES_DTYPE)[:n_local].copy(),
+                         hits.cpu().numpy().view(aln.HIT_DTYPE)[:n_local * hit_cap].reshape(n_local, hit_cap).copy())
     clocks = clk.summary()
+    al.check_status()
     ms_head = float(np.mean(times["persistent"]))
     ms_plain = float(np.mean(times["plain"]))
     ms_head, ms_plain = max_over_ranks([ms_head, ms_plain], ws, dev)
+    for mode in modes:  # the whole batch's results, in read order, on every rank
+        out[mode] = concat_over_ranks(out[mode], ws)
     rp, hp = out["plain"]
     rq, hq = out["persistent"]
     inc = ((rp["flags"] | rq["flags"]) & aln.FLAG_INCOMPLETE) != 0
@@ -771,16 +799,21 @@ def run_gpu(args):
                    "hit_overflow": int(((fl & aln.FLAG_HIT_OVERFLOW) != 0).sum()),
                    "no_hit": int((rq["n_hits"] == 0).sum())}
 
-    # end to end through the public API with host buffers (pinned), copies timed
+    # end to end through the public API with host buffers (pinned), copies timed:
+    # inputs in, the search, aln_compact_hits, then the per-read results, the hit
+    # offsets and exactly the hits written come back (the hit count is read first)
     h_bases = torch.from_numpy(bases.view(np.int32)).pin_memory()
     h_nmask = torch.from_numpy(nmask.view(np.int32)).pin_memory()
     h_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
     h_lens = torch.from_numpy(lens.view(np.int16)).pin_memory()
     h_res = torch.empty(res.numel(), dtype=torch.uint8).pin_memory()
-    h_hits = torch.empty(hits.numel(), dtype=torch.uint8).pin_memory()
+    hit_off = torch.empty(n_local + 1, dtype=torch.int32, device=dev)
+    dense = torch.empty(hits.numel(), dtype=torch.uint8, device=dev)
+    cscratch = al.compact_scratch(n_local)
+    h_off = torch.empty(n_local + 1, dtype=torch.int32).pin_memory()
+    h_dense = torch.empty(hits.numel(), dtype=torch.uint8).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in (h_bases, h_nmask, h_offs, h_lens))
-    d2h = h_res.numel() + h_hits.numel()
-    e2e_ms = []
+    e2e_ms, d2h_list = [], []
     with torch.cuda.stream(stream):
         for it in range(args.warmup + args.steps):
             flush.zero_()
@@ -792,32 +825,54 @@ def run_gpu(args):
             d["offsets"].copy_(h_offs, non_blocking=True)
             d["lens"].copy_(h_lens, non_blocking=True)
             step("persistent")
+            al.compact(res, hits, n_local, hit_cap, hit_off, dense, cscratch, stream)
             h_res.copy_(res, non_blocking=True)
-            h_hits.copy_(hits, non_blocking=True)
+            h_off.copy_(hit_off, non_blocking=True)
+            stream.synchronize()
+            total = int(h_off[n_local])
+            nb = total * aln.HIT_DTYPE.itemsize
+            h_dense[:nb].copy_(dense[:nb], non_blocking=True)
             e1.record(stream)
             e1.synchronize()
             if it >= args.warmup:
                 e2e_ms.append(e0.elapsed_time(e1))
-    e2e_v = ws * n / (np.mean(e2e_ms) / 1000)
+                d2h_list.append(h_res.numel() + h_off.numel() * 4 + nb)
+    d2h = int(np.mean(d2h_list))
+    # the compacted hits are the search's hits
+    rq_l, hq_l = (res.cpu().numpy().view(aln.RES_DTYPE)[:n_local],
+                  hits.cpu().numpy().view(aln.HIT_DTYPE)[:n_local * hit_cap].reshape(n_local, hit_cap))
+    e2e_same = h_dense.numpy()[:total * 16].tobytes() == \
+        hq_l[np.arange(hit_cap)[None, :] < rq_l["n_hits"][:, None]].tobytes()
+    e2e_ms = max_over_ranks([float(np.mean(e2e_ms))], ws, dev)[0]
+    e2e_v = n / (e2e_ms / 1000)
 
     line = {
-        "metric": METRIC, "value": ws * n / (ms_head / 1000), "unit": "reads/s", "n_gpus": ws,
+        "metric": METRIC, "value": n / (ms_head / 1000), "unit": "reads/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_head, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": workload_config(args.workload, w, n, ws),
-        "plain": {"value": ws * n / (ms_plain / 1000), "ms_per_step": ms_plain,
+        "plain": {"value": n / (ms_plain / 1000), "ms_per_step": ms_plain,
                   "bit_identical_to_persistent_on_complete_reads": same},
         "flags": flag_counts,
         "schedule": {"blocks_per_sm": params["persistent"].blocks_per_sm or "max",
-                     "autotune_ms": tuned_ms, "graph_replay": bool(graph is not None)},
-        # per persistent step: D pre-pass, two visit-order kernels, the search
-        # (a graph replay runs the same four kernels)
-        "gpu_launches": args.steps * 4,
-        "e2e": {"value": e2e_v, "unit": "reads/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                     "smem_stack": params["persistent"].smem_stack or 8,
+                     "help_after": params["persistent"].help_after or 4096,
+                     "autotune_ms": tuned_ms, "graph_replay": bool(graph is not None),
+                     "reads_per_rank": [partition_range(n, r, ws)[1] - partition_range(n, r, ws)[0]
+                                        for r in range(ws)]},
+        # timed region: per persistent step the D pre-pass, two visit-order
+        # kernels and the search (a graph replay runs the same four kernels),
+        # per plain step the one search kernel
+        "gpu_launches": args.steps * (4 + 1),
+        "e2e": {"value": e2e_v, "unit": "reads/s", "h2d_bytes_per_step": int(h2d) * ws,
+                "d2h_bytes_per_step": int(d2h) * ws, "hits_compacted": "aln_compact_hits",
+                "compacted_hits_equal_search_hits": bool(e2e_same)},
         "clocks": clocks,
         "build_s": t_build, "gen_s": t_gen,
     }
+    if rank != 0:  # the other replicas are done once their timings and results are in
+        torch.distributed.destroy_process_group()
+        return
     probes = {}
     if args.gather_probe:
         probes["hbm"] = gather_probe_phase(aln, torch, dev, stream)
@@ -963,7 +1018,19 @@ def main():
     ap.add_argument("--human-warmup", type=int, default=3)
     ap.add_argument("--human-serve-seconds", type=float, default=60.0)
     ap.add_argument("--human-serve-lambda", type=float, default=50.0)
+    ap.add_argument("--index-build", default="gpu", choices=["gpu", "host"],
+                    help="build the index with fm_index_build_gpu (default) or on the host cores")
     args = ap.parse_args()
+    if args.gpus > 1 and "RANK" not in os.environ:
+        # one process per GPU: re-launch this command under torch.distributed.run
+        import socket
+        sk = socket.socket()
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+        sk.close()
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+        os.execv(sys.executable, cmd)
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -178,7 +178,13 @@ typedef struct {
     uint8_t smem_stack;     /* persistent form: search-stack entries per lane held in shared
                                memory (the rest in local memory): 0 = 8, else one of
                                ALN_SMEM_STACK_CHOICES; result-neutral */
-    uint8_t reserved0;
+    uint8_t l2_window;      /* persistent form: 1 = launch the search with an L2 access-policy
+                               window over the prefix-trie tables of both texts (persisting
+                               hits, streaming misses), the hottest index data: every search
+                               starts in them.  The first such call on a device raises this
+                               process's persisting-L2 set-aside (cudaLimitPersistingL2CacheSize,
+                               a limit of the CUDA context) to the window size; 0 = off;
+                               result-neutral */
     uint32_t work_limit;    /* node expansions per read before ALN_FLAG_WORK_LIMIT; 0 = 2^24 */
     uint32_t loop_limit;    /* persistent form: trips of the kernel's loop per warp before the
                                warp stops (ALN_STATUS_LOOP_LIMIT, unfinished reads flagged
@@ -188,8 +194,14 @@ typedef struct {
     uint32_t help_after;    /* persistent form: once the lane searching a read has made this
                                many node expansions, lanes of its warp that finish their own
                                reads take its pending subtrees before they take new reads
-                               (the lanes a heavy read gets); 0 = 4096, 0xFFFFFFFF = only
-                               once the read queue is empty; result-neutral */
+                               (the lanes a heavy read gets); 0 or 0xFFFFFFFF = only once
+                               the read queue is empty; result-neutral */
+    uint32_t heavy_after;   /* persistent form with a pre-pass scratch: once the lane owning a
+                               read has made this many expansions, the read is handed to the
+                               heavy phase, which searches it with every lane of the GPU (up to
+                               2048 reads per call; later ones stay with their warp); 0 = 2^18,
+                               0xFFFFFFFF = never; result-neutral */
+    uint32_t reserved;
 } aln_params;
 
 #define ALN_SMEM_STACK_CHOICES {4, 8, 12}
@@ -250,7 +262,10 @@ typedef struct {
  * from the queue the same way without searching it, so every read gets a
  * result; the binding turns the status bit into ALN_ELIMIT.
  * Persistent mode first computes every read's D array in a pre-pass and visits
- * reads in decreasing order of their lower bound.  Its scratch is out->scratch
+ * reads in decreasing order of their lower bound; reads that pass
+ * params.heavy_after expansions are then searched by the heavy phase, one
+ * deepening pass per launch with every lane of the GPU sharing their subtrees
+ * through a task ring.  Its scratch is out->scratch
  * if given, else a block from a memory pool owned by the device index,
  * allocated and freed in stream order by the call.  While stream is being
  * captured into a graph without out->scratch (or if the pool cannot serve) the
@@ -265,8 +280,10 @@ typedef struct {
 int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
                const aln_params *params, aln_result *out, void *stream);
 
-/* Bytes of aln_result.scratch the persistent form uses for n_reads reads
- * (256 + 20 * n_reads).  Host only; never fails. */
+/* Bytes of aln_result.scratch the persistent form uses for n_reads reads:
+ * 256 + 20 * n_reads for the D pre-pass and visit order, rounded up to 256,
+ * plus a fixed block (about 100 MB) for the heavy phase (handed-over reads,
+ * their candidate tables, the task ring).  Host only; never fails. */
 uint64_t aln_search_scratch_bytes(uint32_t n_reads);
 
 /* Autotuner for the persistent form (the scheduler's knobs: how many lanes are
@@ -302,6 +319,81 @@ int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint32_t n_reads
  * n_pos_out are device memory; max_width 1..64.  Asynchronous on stream. */
 int sa_to_pos(const fm_dindex *idx, const aln_hit *hits, uint32_t n_hits, uint32_t max_width,
               uint64_t *pos_out, uint32_t *n_pos_out, void *stream);
+
+/* Dense form of a search's hits, so that what a caller copies back grows with
+ * the hits found rather than with n_reads * hit_cap (Sec. 2: the number of
+ * places a read matches is usually one).  Reads the search's output arrays
+ * (reads: n_reads results, hits: n_reads * hit_cap slots) and writes
+ *   offsets[r] = hits written for reads 0 .. r-1, r = 0 .. n_reads
+ *                (offsets[n_reads] = the total),
+ *   dense[offsets[r] + t] = hits[r * hit_cap + t] for t < reads[r].n_hits,
+ * leaving out any hit whose place is at or past dense_cap (the caller compares
+ * offsets[n_reads] with dense_cap).  All pointers are device memory; scratch:
+ * aln_compact_scratch_bytes(n_reads) bytes, 4-byte aligned.  Asynchronous on
+ * stream.  ALN_EINVAL for null arrays, a small scratch, hit_cap outside
+ * 1..ALN_MAX_HIT_CAP or n_reads * hit_cap >= 2^32. */
+uint64_t aln_compact_scratch_bytes(uint32_t n_reads);
+int aln_compact_hits(const aln_read_result *reads, const aln_hit *hits, uint32_t n_reads, uint32_t hit_cap,
+                     uint32_t *offsets, aln_hit *dense, uint64_t dense_cap, void *scratch, uint64_t scratch_bytes,
+                     void *stream);
+
+/* ---------------------------------------------------------------- pairing
+ *
+ * The pairing stage after the search (Sec. 2 and the pipeline of Sec. 3: the
+ * two mates' hits are combined using the fragment length; the paper gives no
+ * rule, this one is the library's).  Read 2p of a searched batch is mate 1 and
+ * read 2p+1 mate 2 of pair p.
+ *  - Placements of a mate: every position of every hit of its best stratum
+ *    (n_diff == d_best), with the hit's strand, target length and n_diff.  A mate
+ *    is placed iff it has 1 <= c0 <= max_place placements and all of them are
+ *    present (every best hit written and its positions known).
+ *  - A combination (one placement per mate) is FR if the strands differ; its
+ *    insert is (reverse placement's start + target length) - forward placement's
+ *    start.
+ *  - Unique pairs: both mates have c0 == 1 and their combination is FR with
+ *    1 <= insert <= ALN_PAIR_ISIZE_MAX.  Their inserts, sorted as s[0..u-1], give
+ *    q1 = s[u/4], q2 = s[u/2], q3 = s[3u/4] and the window
+ *    [max(1, q1 - 2 (q3 - q1)), min(ALN_PAIR_ISIZE_MAX, q3 + 2 (q3 - q1))];
+ *    with u < 8 the window is [1, ALN_PAIR_ISIZE_MAX] and q1 = q2 = q3 = 0.
+ *  - Proper: FR with the insert inside the window.  The pair's choice is the
+ *    proper combination smallest by (n_diff1 + n_diff2, |insert - q2|, insert,
+ *    pos1, pos2, strand1, len1, len2); with both mates placed and no proper
+ *    combination the pair is discordant (mates from unrelated loci). */
+#define ALN_PAIR_ISIZE_MAX 65535
+#define ALN_PAIR_MAPPED1 0x01    /* mate 1 has a hit */
+#define ALN_PAIR_MAPPED2 0x02
+#define ALN_PAIR_PLACED1 0x04    /* mate 1 is placed */
+#define ALN_PAIR_PLACED2 0x08
+#define ALN_PAIR_UNIQUE 0x10     /* a unique pair (counted in the insert-size estimate) */
+#define ALN_PAIR_PROPER 0x20     /* a proper combination exists; pos, strand, insert hold the choice */
+#define ALN_PAIR_DISCORDANT 0x40 /* both mates placed, no proper combination */
+
+typedef struct {
+    uint64_t pos[2];     /* chosen placement of mate 1 / mate 2 (forward-strand start); ~0 if none */
+    uint32_t insert;     /* its insert size; 0 if none */
+    uint16_t n_proper;   /* proper combinations (saturating at 65535) */
+    uint8_t strand[2];   /* 0 forward, 1 reverse; 255 if none */
+    uint8_t flags;       /* ALN_PAIR_* */
+    uint8_t reserved[7];
+} aln_pair_result;       /* 32 bytes */
+
+typedef struct {
+    uint32_t n_unique, q1, q2, q3, lo, hi; /* unique pairs, insert quartiles, window */
+    uint32_t reserved[2];
+} aln_pair_stats;
+
+/* Pair the mates of n_pairs pairs from a search of their 2 * n_pairs reads:
+ * reads (the search's results), hit_off / hits (its hits compacted by
+ * aln_compact_hits: n_reads + 1 offsets, dense hits), pos / npos (sa_to_pos of
+ * those dense hits with max_width).  Writes out[n_pairs] and *stats (device).
+ * max_place: 1..max_width (<= 64).  scratch: aln_pair_scratch_bytes() bytes of
+ * device memory.  All pointers device memory; asynchronous on stream.
+ * ALN_EINVAL for null arrays or sizes out of range. */
+uint64_t aln_pair_scratch_bytes(void);
+int aln_pair_resolve(const aln_read_result *reads, const uint32_t *hit_off, const aln_hit *hits,
+                     const uint64_t *pos, const uint32_t *npos, uint32_t max_width, uint32_t n_pairs,
+                     uint32_t max_place, aln_pair_result *out, aln_pair_stats *stats, void *scratch,
+                     uint64_t scratch_bytes, void *stream);
 
 /* ---------------------------------------------------------------- serving
  *
@@ -363,7 +455,8 @@ void aln_server_destroy(aln_server *s);
  *
  * aln_search_noalloc runs the persistent search (params.mode is ignored) exactly
  * as aln_search does and writes the same results into the caller's buffers
- * (out->scratch is not used: the search scans D in its own loop).
+ * (out->scratch and params.l2_window are not used: the search scans D in its
+ * own loop and sets no access-policy window).
  * Its only scratch, the device work-queue counter, lives in a fixed array of
  * ALN_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that loads
  * the library holds until the process exits.  The call allocates nothing.

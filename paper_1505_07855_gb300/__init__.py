@@ -25,7 +25,8 @@ from ._lib import (  # noqa: F401
     FLAG_INCOMPLETE, FLAG_LOOP_LIMIT, FLAG_READ_TOO_LONG, FLAG_STACK_OVERFLOW, FLAG_WORK_LIMIT,
     HIT_DTYPE, MAX_HIT_CAP, MAX_READ_LEN, MAX_Z, MODE_PERSISTENT, MODE_PLAIN, POS_BAD_HIT,
     POS_TOO_WIDE, POS_WALK_LIMIT, RES_DTYPE, SMEM_STACK_CHOICES, STATUS_LOOP_LIMIT, STRATA_BEST1,
-    STRATA_FULL, check, lib, library_path,
+    STRATA_FULL, check, lib, library_path, PAIR_DTYPE, PAIR_MAPPED1, PAIR_MAPPED2, PAIR_PLACED1, PAIR_PLACED2,
+    PAIR_UNIQUE, PAIR_PROPER, PAIR_DISCORDANT, PAIR_STATS_FIELDS,
 )
 
 __all__ = ["Index", "DeviceIndex", "Params", "Aligner", "pack_reads", "gather_probe", "scratch_bytes",
@@ -169,12 +170,14 @@ class Params:
     smem_stack: int = 0
     loop_limit: int = 0
     help_after: int = 0
+    l2_window: int = 0
+    heavy_after: int = 0
 
     def c(self) -> _lib.aln_params:
         return _lib.aln_params(self.z, self.max_gapo, self.max_gape, self.seed_len, self.seed_z,
                                self.indel_end_skip, self.hit_cap, self.mode, self.strata,
-                               self.blocks_per_sm, self.smem_stack, 0, self.work_limit,
-                               self.loop_limit, self.help_after)
+                               self.blocks_per_sm, self.smem_stack, self.l2_window, self.work_limit,
+                               self.loop_limit, self.help_after, self.heavy_after, 0)
 
     @classmethod
     def from_limits(cls, lim: dict, **kw) -> "Params":
@@ -293,6 +296,46 @@ class Aligner:
         r = res.cpu().numpy().view(RES_DTYPE)[:n]
         h = hits.cpu().numpy().view(HIT_DTYPE)[:n * params.hit_cap].reshape(n, params.hit_cap)
         return r, h
+
+    def compact(self, res, hits, n: int, hit_cap: int, offsets, dense, scratch, stream=None) -> None:
+        """aln_compact_hits on device buffers: offsets (n + 1 uint32), dense hits
+        (its capacity is its size in hits), scratch (aln_compact_scratch_bytes)."""
+        check(lib().aln_compact_hits(_ptr(res), _ptr(hits), n, hit_cap, _ptr(offsets), _ptr(dense),
+                                     dense.numel() * dense.element_size() // HIT_DTYPE.itemsize, _ptr(scratch),
+                                     scratch.numel() * scratch.element_size(), _stream_ptr(stream)),
+              "aln_compact_hits")
+
+    def compact_scratch(self, n: int):
+        """A device buffer for aln_compact_hits' scratch."""
+        t = self.torch
+        return t.empty(int(lib().aln_compact_scratch_bytes(n)), dtype=t.uint8, device=self.dev)
+
+    def pair(self, res, n_reads: int, hit_cap: int, hits, max_width: int = 16, max_place: int = 16,
+             stream=None):
+        """Pairing of reads 2p / 2p+1 from a search's device outputs (res, hits):
+        aln_compact_hits, sa_to_pos of the dense hits, aln_pair_resolve.
+        Returns numpy (pairs PAIR_DTYPE[n_reads // 2], stats dict)."""
+        t = self.torch
+        n_pairs = n_reads // 2
+        off = t.empty(n_reads + 1, dtype=t.int32, device=self.dev)
+        dense = t.empty(max(1, n_reads * hit_cap) * HIT_DTYPE.itemsize, dtype=t.uint8, device=self.dev)
+        self.compact(res, hits, n_reads, hit_cap, off, dense, self.compact_scratch(n_reads), stream)
+        t.cuda.synchronize(self.dev)
+        total = int(off[n_reads].item())
+        pos = t.empty(max(1, total * max_width), dtype=t.int64, device=self.dev)
+        npos = t.empty(max(1, total), dtype=t.int32, device=self.dev)
+        if total:
+            self.dix.sa_to_pos(dense, total, max_width, pos, npos, stream)
+        out = t.empty(max(1, n_pairs) * PAIR_DTYPE.itemsize, dtype=t.uint8, device=self.dev)
+        stats = t.zeros(8, dtype=t.int32, device=self.dev)
+        scratch = t.empty(int(lib().aln_pair_scratch_bytes()), dtype=t.uint8, device=self.dev)
+        check(lib().aln_pair_resolve(_ptr(res), _ptr(off), _ptr(dense), _ptr(pos), _ptr(npos), max_width, n_pairs,
+                                     max_place, _ptr(out), _ptr(stats), _ptr(scratch),
+                                     scratch.numel(), _stream_ptr(stream)), "aln_pair_resolve")
+        t.cuda.synchronize(self.dev)
+        st = stats.cpu().numpy().view(np.uint32)
+        return (out.cpu().numpy().view(PAIR_DTYPE)[:n_pairs].copy(),
+                dict(zip(PAIR_STATS_FIELDS, (int(x) for x in st[:6]))))
 
     def positions(self, hits_np: np.ndarray, max_width: int = 16, stream=None):
         """sa_to_pos for a host array of hits; returns (pos[n, max_width], npos[n])."""

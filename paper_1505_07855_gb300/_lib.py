@@ -36,6 +36,12 @@ POS_TOO_WIDE = 0xFFFFFFFF
 POS_WALK_LIMIT = 0xFFFFFFFE
 POS_BAD_HIT = 0xFFFFFFFD
 
+PAIR_MAPPED1, PAIR_MAPPED2, PAIR_PLACED1, PAIR_PLACED2 = 0x01, 0x02, 0x04, 0x08
+PAIR_UNIQUE, PAIR_PROPER, PAIR_DISCORDANT = 0x10, 0x20, 0x40
+PAIR_DTYPE = np.dtype([("pos", "<u8", (2,)), ("insert", "<u4"), ("n_proper", "<u2"), ("strand", "u1", (2,)),
+                       ("flags", "u1"), ("reserved", "u1", (7,))])
+PAIR_STATS_FIELDS = ("n_unique", "q1", "q2", "q3", "lo", "hi")
+
 # numpy views of aln_hit (16 B) and aln_read_result (12 B)
 HIT_DTYPE = np.dtype([("k", "<u4"), ("l", "<u4"), ("aligned_len", "<u2"), ("strand", "u1"),
                       ("n_diff", "u1"), ("n_mm", "u1"), ("n_gapo", "u1"), ("n_gape", "u1"),
@@ -68,8 +74,9 @@ class aln_params(ctypes.Structure):
                 ("indel_end_skip", ctypes.c_uint8), ("hit_cap", ctypes.c_uint8),
                 ("mode", ctypes.c_uint8), ("strata", ctypes.c_uint8),
                 ("blocks_per_sm", ctypes.c_uint8), ("smem_stack", ctypes.c_uint8),
-                ("reserved0", ctypes.c_uint8), ("work_limit", ctypes.c_uint32),
-                ("loop_limit", ctypes.c_uint32), ("help_after", ctypes.c_uint32)]
+                ("l2_window", ctypes.c_uint8), ("work_limit", ctypes.c_uint32),
+                ("loop_limit", ctypes.c_uint32), ("help_after", ctypes.c_uint32),
+                ("heavy_after", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class aln_result(ctypes.Structure):
@@ -91,9 +98,10 @@ class aln_server_stats_t(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("n_slots", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
-assert ctypes.sizeof(aln_params) == 24 and ctypes.sizeof(fm_build_opts) == 24
+assert ctypes.sizeof(aln_params) == 32 and ctypes.sizeof(fm_build_opts) == 24
+assert PAIR_DTYPE.itemsize == 32
 assert ctypes.sizeof(fm_index_info_t) == 120 and ctypes.sizeof(aln_result) == 40
-assert ctypes.sizeof(aln_server_config) == 64 and ctypes.sizeof(aln_server_stats_t) == 72
+assert ctypes.sizeof(aln_server_config) == 72 and ctypes.sizeof(aln_server_stats_t) == 72
 
 # name -> (restype, argtypes); the exported ABI
 P, u8p = ctypes.c_void_p, ctypes.c_void_p
@@ -112,6 +120,12 @@ SIGNATURES = {
                                   ctypes.POINTER(aln_params), ctypes.POINTER(aln_result), P]),
     "aln_search_scratch_bytes": (ctypes.c_uint64, [ctypes.c_uint32]),
     "sa_to_pos": (ctypes.c_int, [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
+    "aln_compact_scratch_bytes": (ctypes.c_uint64, [ctypes.c_uint32]),
+    "aln_pair_scratch_bytes": (ctypes.c_uint64, []),
+    "aln_pair_resolve": (ctypes.c_int, [P, P, P, P, P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, P, P,
+                                        ctypes.c_uint64, P]),
+    "aln_compact_hits": (ctypes.c_int, [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, ctypes.c_uint64, P,
+                                        ctypes.c_uint64, P]),
     "aln_autotune": (ctypes.c_int, [P, ctypes.POINTER(aln_batch), ctypes.c_uint32, ctypes.POINTER(aln_params),
                                     ctypes.POINTER(aln_result), P, ctypes.POINTER(ctypes.c_float)]),
     "aln_search_noalloc": (ctypes.c_int, [P, ctypes.POINTER(aln_batch), ctypes.c_uint32,

@@ -17,9 +17,9 @@ LIB = os.path.join(BUILD, "libaln_gb300.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["aln_kernels.cu", "aln_capi.cu", "index_gpu.cu"]
+CU_SOURCES = ["aln_kernels.cu", "aln_capi.cu", "index_gpu.cu", "aln_pair.cu"]
 CPP_SOURCES = ["index_build.cpp", "aln_server.cpp"]
-HEADERS = ["aln_device.cuh", "aln_search.cuh", "aln_flat.cuh", "aln_internal.h"]
+HEADERS = ["aln_device.cuh", "aln_search.cuh", "aln_flat.cuh", "aln_internal.h", "aln_scan.cuh"]
 
 
 def _newer(target: str, deps: list[str]) -> bool:

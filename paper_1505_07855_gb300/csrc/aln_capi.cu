@@ -10,6 +10,7 @@
 
 #include "aln_device.cuh"
 #include "aln_internal.h"
+#include "aln_scan.cuh"
 #include "aln_search.cuh"
 
 namespace aln {
@@ -31,6 +32,8 @@ struct fm_dindex {
     DIndex X{};
     fm_index_info_t info{};
     void *mem[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    void *kmer_all = nullptr;             // prefix-trie tables of both texts, one buffer (L2 window)
+    uint64_t kmer_bytes = 0;
     uint32_t *queues = nullptr;           // persistent-mode queue counters: ring, then reserved
     std::atomic<uint32_t> next_queue{0};
     std::atomic<uint32_t> next_capture{0};
@@ -57,6 +60,11 @@ static int search_params(const char *who, const aln_params &P, uint32_t n_reads,
     sp.blocks_per_sm = P.blocks_per_sm;
     sp.smem_stack = P.smem_stack;
     sp.help_after = P.help_after ? P.help_after : kDefaultHelpAfter;
+    sp.heavy_after = P.heavy_after ? P.heavy_after : kDefaultHeavyAfter;
+    sp.heavy.hdr = nullptr;
+    if (P.l2_window > 1) return fail(ALN_EINVAL, std::string(who) + ": l2_window must be 0 or 1");
+    sp.window_base = nullptr;
+    sp.window_bytes = 0;
     if (P.loop_limit) {
         sp.loop_limit = P.loop_limit;
     } else {  // 64 * n_reads * (576 + work_limit), saturating at 2^62
@@ -83,6 +91,7 @@ extern "C" void fm_dindex_free(fm_dindex *d) {
         for (void *p : row)
             if (p) cudaFree(p);
     if (d->queues) cudaFree(d->queues);
+    if (d->kmer_all) cudaFree(d->kmer_all);
     if (d->pool) cudaMemPoolDestroy(d->pool);
     cudaSetDevice(prev);
     tune_forget(d);
@@ -108,10 +117,21 @@ extern "C" int fm_index_to_device(const fm_index *idx, int device, void *stream,
     while ((1u << sh) < idx->sa_sample) sh++;
     d->X.sa_shift = sh;
     int rc = ALN_OK;
+    // both prefix-trie tables in one buffer, so that one L2 access-policy window covers them
+    d->kmer_bytes = (idx->t[0].kmer.size() + idx->t[1].kmer.size()) * 4;
+    if (d->kmer_bytes) {
+        if ((e = cudaMalloc(&d->kmer_all, d->kmer_bytes)) != cudaSuccess) rc = cuda_fail(e, "fm_index_to_device: cudaMalloc");
+        for (int w = 0; w < 2 && rc == ALN_OK; w++) {
+            char *dst = static_cast<char *>(d->kmer_all) + (w ? idx->t[0].kmer.size() * 4 : 0);
+            if ((e = cudaMemcpyAsync(dst, idx->t[w].kmer.data(), idx->t[w].kmer.size() * 4, cudaMemcpyHostToDevice,
+                                     st)) != cudaSuccess)
+                rc = cuda_fail(e, "fm_index_to_device: copy");
+        }
+    }
     for (int w = 0; w < 2 && rc == ALN_OK; w++) {
         const HostText &T = idx->t[w];
-        const void *src[3] = {T.blocks.data(), T.sa_samp.data(), T.kmer.data()};
-        const size_t bytes[3] = {T.blocks.size() * 4, T.sa_samp.size() * 4, T.kmer.size() * 4};
+        const void *src[3] = {T.blocks.data(), T.sa_samp.data(), nullptr};
+        const size_t bytes[3] = {T.blocks.size() * 4, T.sa_samp.size() * 4, 0};
         for (int a = 0; a < 3 && rc == ALN_OK; a++) {
             if (!bytes[a]) continue;
             if ((e = cudaMalloc(&d->mem[w][a], bytes[a])) != cudaSuccess) rc = cuda_fail(e, "fm_index_to_device: cudaMalloc");
@@ -121,7 +141,9 @@ extern "C" int fm_index_to_device(const fm_index *idx, int device, void *stream,
         DText &D = d->X.t[w];
         D.blocks = static_cast<const uint4 *>(d->mem[w][0]);
         D.sa_samp = static_cast<const uint32_t *>(d->mem[w][1]);
-        D.kmer = static_cast<const uint2 *>(d->mem[w][2]);
+        D.kmer = d->kmer_bytes ? reinterpret_cast<const uint2 *>(static_cast<const char *>(d->kmer_all) +
+                                                                (w ? idx->t[0].kmer.size() * 4 : 0))
+                               : nullptr;
         for (int c = 0; c < 4; c++) D.C1[c] = static_cast<uint32_t>(T.C[c] + 1);
         D.C1[4] = static_cast<uint32_t>(T.n + 1);
         D.primary = static_cast<uint32_t>(T.primary);
@@ -165,6 +187,34 @@ extern "C" int fm_dindex_info(const fm_dindex *d, fm_index_info_t *info) {
 
 extern "C" uint64_t aln_search_scratch_bytes(uint32_t n_reads) { return search_scratch_bytes(n_reads); }
 
+// The L2 access-policy window over the prefix-trie tables of both texts: at most
+// the device's largest window, and the context's persisting-L2 set-aside raised
+// to that size if it is smaller (a limit of this process's context).
+static int l2_window_for(fm_dindex *d, SearchParams &sp) {
+    static std::mutex mu;
+    static uint64_t set_aside[64] = {};
+    int max_window = 0, max_persist = 0;
+    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, d->device);
+    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, d->device);
+    if (max_window <= 0 || max_persist <= 0) return ALN_OK;  // not supported: no window
+    uint64_t bytes = d->kmer_bytes;
+    if (bytes > static_cast<uint64_t>(max_window)) bytes = static_cast<uint64_t>(max_window);
+    const uint64_t want = bytes < static_cast<uint64_t>(max_persist) ? bytes : static_cast<uint64_t>(max_persist);
+    if (d->device >= 0 && d->device < 64) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (set_aside[d->device] < want) {
+            const cudaError_t e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+            if (e != cudaSuccess) return cuda_fail(e, "aln_search: persisting L2 set-aside");
+            set_aside[d->device] = want;
+        }
+        sp.window_base = d->kmer_all;
+        sp.window_bytes = bytes;
+        sp.window_hit_ratio = static_cast<float>(static_cast<double>(set_aside[d->device]) / static_cast<double>(bytes));
+        if (sp.window_hit_ratio > 1.0f) sp.window_hit_ratio = 1.0f;
+    }
+    return ALN_OK;
+}
+
 extern "C" int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads, const aln_params *params,
                           aln_result *out, void *stream) {
     if (!idx || !batch || !params || !out) return fail(ALN_EINVAL, "aln_search: null argument");
@@ -184,6 +234,13 @@ extern "C" int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != idx->device) cudaSetDevice(idx->device);
+    if (P.l2_window && P.mode == ALN_MODE_PERSISTENT && d->kmer_bytes) {
+        rc = l2_window_for(d, sp);
+        if (rc != ALN_OK) {
+            if (prev != idx->device) cudaSetDevice(prev);
+            return rc;
+        }
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
@@ -292,7 +349,7 @@ extern "C" int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint3
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = ALN_OK, best_b = 0, best_s = 0;
-    uint32_t best_h = params->help_after;
+    uint32_t best_h = params->help_after ? params->help_after : kDefaultHelpAfter;  // what the first sweep ran with
     float best = 0;
     auto timed = [&](float *ms) {
         cudaEventRecord(e0, st);
@@ -321,7 +378,7 @@ extern "C" int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint3
             }
         }
     }
-    static const uint32_t kHelp[] = {1024u, 4096u, 16384u, 0xFFFFFFFFu};
+    static const uint32_t kHelp[] = {1024u, 4096u, 16384u, 0xFFFFFFFFu};  // the first sweep ran with the given value
     p.blocks_per_sm = static_cast<uint8_t>(best_b);
     p.smem_stack = static_cast<uint8_t>(best_s);
     for (uint32_t h : kHelp) {
@@ -440,6 +497,55 @@ extern "C" int sa_to_pos(const fm_dindex *idx, const aln_hit *hits, uint32_t n_h
     cudaError_t e = cudaGetLastError();
     if (prev != idx->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(e, "sa_to_pos: launch");
+    return ALN_OK;
+}
+
+// ---------------------------------------------------------------- aln_compact_hits
+
+namespace aln {
+
+__global__ void hit_count_kernel(const aln_read_result *reads, uint32_t n, uint32_t *offsets) {
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r <= n;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        offsets[r] = r < n ? reads[r].n_hits : 0u;
+}
+
+// One thread per read: its written hits to their place in the dense array.
+__global__ void hit_gather_kernel(const aln_read_result *reads, const aln_hit *hits, uint32_t n, uint32_t hit_cap,
+                                  const uint32_t *offsets, aln_hit *dense, uint64_t dense_cap) {
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < n;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t k = reads[r].n_hits < hit_cap ? reads[r].n_hits : hit_cap;
+        const uint64_t o = offsets[r];
+        for (uint32_t t = 0; t < k && o + t < dense_cap; t++) dense[o + t] = hits[r * hit_cap + t];
+    }
+}
+
+}  // namespace aln
+
+extern "C" uint64_t aln_compact_scratch_bytes(uint32_t n_reads) {
+    return 4ull * scan::scan_temp_words(static_cast<uint64_t>(n_reads) + 1);
+}
+
+extern "C" int aln_compact_hits(const aln_read_result *reads, const aln_hit *hits, uint32_t n_reads, uint32_t hit_cap,
+                                uint32_t *offsets, aln_hit *dense, uint64_t dense_cap, void *scratch,
+                                uint64_t scratch_bytes, void *stream) {
+    if (!offsets || (n_reads && (!reads || !hits)) || (dense_cap && !dense) || !scratch)
+        return fail(ALN_EINVAL, "aln_compact_hits: null argument");
+    if (hit_cap < 1 || hit_cap > ALN_MAX_HIT_CAP) return fail(ALN_EINVAL, "aln_compact_hits: hit_cap must be 1..255");
+    if (scratch_bytes < aln_compact_scratch_bytes(n_reads))
+        return fail(ALN_EINVAL, "aln_compact_hits: scratch smaller than aln_compact_scratch_bytes");
+    if (static_cast<uint64_t>(n_reads) * hit_cap > 0xFFFFFFFFull)
+        return fail(ALN_EINVAL, "aln_compact_hits: n_reads * hit_cap must be below 2^32");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint64_t m = static_cast<uint64_t>(n_reads) + 1;
+    const unsigned g = static_cast<unsigned>((m + 255) / 256 < 65536 ? (m + 255) / 256 : 65536);
+    hit_count_kernel<<<g, 256, 0, st>>>(reads, n_reads, offsets);
+    scan::device_scan(offsets, offsets, m, false, static_cast<uint32_t *>(scratch), st, scan::OpAdd());
+    if (n_reads)
+        hit_gather_kernel<<<g, 256, 0, st>>>(reads, hits, n_reads, hit_cap, offsets, dense, dense_cap);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "aln_compact_hits: launch");
     return ALN_OK;
 }
 

@@ -28,6 +28,9 @@ namespace aln {
 enum : uint32_t { PH_IDLE = 0, PH_DSCAN = 1, PH_DFS = 2, PH_DONE = 3, PH_FREE = 4, PH_WAIT = 5, PH_RETURN = 6 };
 enum : uint32_t { ROLE_OWN = 0, ROLE_HELP = 1 };
 enum : uint32_t { F_NONE = 0, F_OCC = 1, F_TABLE = 2, F_ROOT = 3, F_ZERO = 4 };
+// lane-private flag bits above the ABI's (never written to a result)
+constexpr uint32_t kFlagHeavyTried = 0x100;  // the read asked for a heavy-phase slot
+constexpr uint32_t kFlagDemoted = 0x200;     // the read was handed to the heavy phase
 constexpr int kSmemStackDefault = 8;  // bottom stack entries per lane kept in shared memory
 
 // First entry of level j (strings of length j) in the prefix-trie table.
@@ -399,6 +402,10 @@ struct FlatLane {
                     start_strand(n, 1);
                     continue;
                 }
+                if (flags & kFlagDemoted) {  // the heavy phase searches it and writes the result
+                    phase = PH_IDLE;
+                    continue;
+                }
                 if ((flags & ALN_FLAG_WORK_LIMIT) || p.strata == ALN_STRATA_FULL) {
                     write_result(res, hits, p, nc > 0, z);
                     continue;
@@ -421,6 +428,21 @@ struct FlatLane {
                 start_pass(n, F);
                 continue;
             }
+            if (role == ROLE_OWN && work > p.heavy_after && p.heavy.hdr && !(flags & kFlagHeavyTried)) {
+                flags |= kFlagHeavyTried;  // hand the read to the heavy phase if it has room
+                const uint32_t hid = atomicAdd(&p.heavy.hdr->n_heavy, 1u);
+                if (hid < kHeavyReads) {
+                    HeavyRead *H = p.heavy.reads + hid;
+                    H->r = r;
+                    H->z = z;
+                    H->m = m;
+                    flags |= kFlagDemoted;
+                    sp = base;
+                    has_next = false;
+                    s = 1;
+                    continue;
+                }
+            }
             if (++work > p.work_limit) {
                 flags |= ALN_FLAG_WORK_LIMIT;
                 sp = base;
@@ -428,60 +450,65 @@ struct FlatLane {
                 if (role == ROLE_OWN) s = 1;
                 continue;
             }
-            uint4 e;
-            if (has_next) {
-                e = next;
-                has_next = false;
-            } else {
-                e = stk_get(--sp);
-            }
-#ifdef ALN_STATS
-            st_pops++;
-#endif
-            const uint32_t info = e.z;
-            const uint32_t i = info & 0xFFu, mm = (info >> 8) & 7u, go = (info >> 11) & 7u, ge = (info >> 14) & 7u;
-            const uint32_t ni = (info >> 17) & 7u, sd = (info >> 20) & 7u, last = (info >> 23) & 3u;
-            const uint32_t diffs = mm + go + ge;
-            const uint32_t rem = B - diffs;
-            if (i == m) {
-                const uint32_t alen = m + (go + ge - ni) - ni;
-                if (alen >= 1)
-                    add_cand(e.x, e.y, (s << 31) | (diffs << 28) | (go << 24) | (ge << 20) | (mm << 16) | alen);
-                continue;
-            }
-            const uint32_t bp0 = s ? bpb0 : bpa0, bp1 = s ? bpb1 : bpa1;
-            const bool isN = rv.isN(i);
-            const uint32_t qi = rv.base(i) ^ (s ? 3u : 0u);
-            const uint32_t Dn = d_at(bp0, bp1, i + 1), Di = d_at(bp0, bp1, i);
-            const uint32_t e1 = p.e < 1 ? 1 : p.e;
-            const bool in_seed = p.seed_len && i < p.seed_len;
-            const bool alt = rem >= 1 && (!in_seed || sd < p.seed_z);
-            const bool allowM = !isN && rem >= Dn;
-            const bool mm_ok = alt && rem - 1 >= Dn;
-            const bool ins_ok = alt && rem - 1 >= Dn && i >= p.e && i + 1 + p.e <= m && last != OP_D &&
-                                (last == OP_I ? ge < p.max_gape : go < p.max_gapo);
-            const bool del_ok = alt && rem - 1 >= Di && i >= e1 && i + e1 <= m && last != OP_I &&
-                                (last == OP_D ? ge < p.max_gape : go < p.max_gapo);
-            const uint32_t L = i + go + ge - 2 * ni;  // target length: consumed + deleted - inserted
-            cur = e;
-            cbits = (allowM ? 1u : 0u) | (mm_ok ? 2u : 0u) | (ins_ok ? 4u : 0u) | (del_ok ? 8u : 0u) | (qi << 4) |
-                    (isN ? 64u : 0u) | (in_seed ? 128u : 0u) | (L < K ? 256u : 0u);
-            if (!(allowM || mm_ok || del_ok || ins_ok)) continue;
-            fr.text = s ? 0u : 1u;  // strand 0 searches X reversed, strand 1 searches X
-            if (!(allowM || mm_ok || del_ok)) {
-                fr.kind = F_ZERO;  // only the insertion child: no extension needed
-            } else if (L == 0) {
-                fr.kind = F_ROOT;
-            } else if (L < K) {
-                fr.kind = F_TABLE;
-                fr.toff = trie_off(L + 1) + (e.w << 2);
-            } else {
-                fr.kind = F_OCC;
-                fr.lo = e.x;
-                fr.hi = e.y;
-            }
-            return;
+            if (expand_top(p, fr)) return;
         }
+    }
+
+    // Pop the top node and decide its children: false if nothing needs fetching
+    // (an emitted hit, or every child pruned), true with fr filled otherwise.
+    __device__ __forceinline__ bool expand_top(const SearchParams &p, FetchReq &fr) {
+        uint4 e;
+        if (has_next) {
+            e = next;
+            has_next = false;
+        } else {
+            e = stk_get(--sp);
+        }
+#ifdef ALN_STATS
+        st_pops++;
+#endif
+        const uint32_t info = e.z;
+        const uint32_t i = info & 0xFFu, mm = (info >> 8) & 7u, go = (info >> 11) & 7u, ge = (info >> 14) & 7u;
+        const uint32_t ni = (info >> 17) & 7u, sd = (info >> 20) & 7u, last = (info >> 23) & 3u;
+        const uint32_t diffs = mm + go + ge;
+        const uint32_t rem = B - diffs;
+        if (i == m) {
+            const uint32_t alen = m + (go + ge - ni) - ni;
+            if (alen >= 1) add_cand(e.x, e.y, (s << 31) | (diffs << 28) | (go << 24) | (ge << 20) | (mm << 16) | alen);
+            return false;
+        }
+        const uint32_t bp0 = s ? bpb0 : bpa0, bp1 = s ? bpb1 : bpa1;
+        const bool isN = rv.isN(i);
+        const uint32_t qi = rv.base(i) ^ (s ? 3u : 0u);
+        const uint32_t Dn = d_at(bp0, bp1, i + 1), Di = d_at(bp0, bp1, i);
+        const uint32_t e1 = p.e < 1 ? 1 : p.e;
+        const bool in_seed = p.seed_len && i < p.seed_len;
+        const bool alt = rem >= 1 && (!in_seed || sd < p.seed_z);
+        const bool allowM = !isN && rem >= Dn;
+        const bool mm_ok = alt && rem - 1 >= Dn;
+        const bool ins_ok = alt && rem - 1 >= Dn && i >= p.e && i + 1 + p.e <= m && last != OP_D &&
+                            (last == OP_I ? ge < p.max_gape : go < p.max_gapo);
+        const bool del_ok = alt && rem - 1 >= Di && i >= e1 && i + e1 <= m && last != OP_I &&
+                            (last == OP_D ? ge < p.max_gape : go < p.max_gapo);
+        const uint32_t L = i + go + ge - 2 * ni;  // target length: consumed + deleted - inserted
+        cur = e;
+        cbits = (allowM ? 1u : 0u) | (mm_ok ? 2u : 0u) | (ins_ok ? 4u : 0u) | (del_ok ? 8u : 0u) | (qi << 4) |
+                (isN ? 64u : 0u) | (in_seed ? 128u : 0u) | (L < K ? 256u : 0u);
+        if (!(allowM || mm_ok || del_ok || ins_ok)) return false;
+        fr.text = s ? 0u : 1u;  // strand 0 searches X reversed, strand 1 searches X
+        if (!(allowM || mm_ok || del_ok)) {
+            fr.kind = F_ZERO;  // only the insertion child: no extension needed
+        } else if (L == 0) {
+            fr.kind = F_ROOT;
+        } else if (L < K) {
+            fr.kind = F_TABLE;
+            fr.toff = trie_off(L + 1) + (e.w << 2);
+        } else {
+            fr.kind = F_OCC;
+            fr.lo = e.x;
+            fr.hi = e.y;
+        }
+        return true;
     }
 
     // Warp-synchronous hand-over, once per trip, all 32 lanes: returning helpers
@@ -556,6 +583,13 @@ struct FlatLane {
                     rv = own_rv;
                 }
             }
+        }
+        // helpers of a read just handed to the heavy phase drop their subtrees
+        const unsigned dem = __ballot_sync(FULL, role == ROLE_OWN && (flags & kFlagDemoted));
+        if (dem && role == ROLE_HELP && ((dem >> owner) & 1u) && phase == PH_DFS) {
+            sp = base;
+            has_next = false;
+            nc = 0;
         }
         const bool can_give = phase == PH_DFS && (sp - base >= 2 || (sp - base >= 1 && has_next));
         unsigned donm = __ballot_sync(FULL, can_give);

@@ -150,6 +150,408 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
 #endif
 }
 
+// ---------------------------------------------------------------- heavy phase
+//
+// Reads whose owner lane passed heavy_after expansions were handed over by the
+// persistent search (kFlagDemoted) and are searched here by every lane of the
+// GPU, one deepening pass per launch: a pass's subtrees are tasks in a ring in
+// global memory; a lane takes a task, searches it depth first (sharing it with
+// the idle lanes of its warp exactly as the persistent search does), gives its
+// bottom stack entries back to the ring while the ring runs low, and merges the
+// candidates it found into the read's hash table (least witness per interval by
+// atomicMin).  After each pass one block per read applies the iterative
+// deepening rule to the table and either writes the result or starts the next
+// pass.  The hit set, witnesses and counts are those of the other forms.
+
+__device__ __forceinline__ uint32_t vload(const uint32_t *p) { return *reinterpret_cast<const volatile uint32_t *>(p); }
+
+// Task t is published once its slot is written: ready[t % cap] = t + 1.
+__device__ __forceinline__ void heavy_push(const HeavyCtx &H, const uint4 &node, uint32_t hid, uint32_t s) {
+    atomicAdd(&H.hdr->outstanding, 1u);
+    const uint32_t t = atomicAdd(&H.hdr->tail, 1u);
+    HeavyTask task;
+    task.node = node;
+    task.hid = hid;
+    task.s = s;
+    task.pad0 = task.pad1 = 0;
+    H.pool[t % kHeavyPool] = task;
+    __threadfence();
+    atomicExch(&H.ready[t % kHeavyPool], t + 1u);
+}
+
+__device__ __forceinline__ unsigned long long mix_id(unsigned long long x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33;
+    return x;
+}
+
+// Insert candidate (lo, hi) of strand s with witness key; returns false if the
+// read's table for that strand is full.
+__device__ bool heavy_insert(const HeavyCtx &H, uint32_t hid, uint32_t s, uint32_t lo, uint32_t hi, uint32_t key) {
+    HeavySlot *T = H.slots + (static_cast<uint64_t>(hid) * 2 + s) * kHeavySlots;
+    const unsigned long long id = (static_cast<unsigned long long>(lo) << 32) | hi;
+    uint32_t j = static_cast<uint32_t>(mix_id(id)) & (kHeavySlots - 1);
+    for (uint32_t probe = 0; probe < kHeavySlots; probe++, j = (j + 1) & (kHeavySlots - 1)) {
+        const unsigned long long old = atomicCAS(&T[j].id, 0ull, id);
+        if (old == 0ull || old == id) {
+            atomicMin(&T[j].key, key);
+            if (old == 0ull) atomicAdd(&H.reads[hid].distinct[s], 1u);
+            return true;
+        }
+    }
+    return false;
+}
+
+// One block per handed-over read: its first pass budget, cleared tables, the
+// root of each strand the lower bound admits as a task.
+__global__ void aln_heavy_start_kernel(SearchParams p, const uint2 *dbp, uint32_t n_text) {
+    const HeavyCtx H = p.heavy;
+    const uint32_t hid = blockIdx.x;
+    if (hid >= min(H.hdr->n_heavy, kHeavyReads)) return;
+    HeavySlot *T = H.slots + static_cast<uint64_t>(hid) * 2 * kHeavySlots;
+    for (uint32_t j = threadIdx.x; j < 2 * kHeavySlots; j += blockDim.x) {
+        T[j].id = 0ull;
+        T[j].key = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        HeavyRead *R = H.reads + hid;
+        const uint2 a = dbp[2ull * R->r], b = dbp[2ull * R->r + 1];
+        const uint32_t d0 = d_at(a.x, a.y, 0), d1 = d_at(b.x, b.y, 0);
+        const uint32_t lb = min(d0, d1);
+        R->B = p.strata == ALN_STRATA_FULL ? R->z : min(R->z, lb + 1);
+        R->state = 0;
+        R->flags = 0;
+        R->distinct[0] = R->distinct[1] = 0;
+        const uint4 root = make_uint4(0, n_text + 1, pack_info(0, 0, 0, 0, 0, 0, OP_M), 0);
+        if (d0 <= R->B) heavy_push(H, root, hid, 0);
+        if (d1 <= R->B) heavy_push(H, root, hid, 1);
+    }
+}
+
+template <int STACK_CAP>
+__global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy_pass_kernel(DIndex X, ReadBatch rb,
+                                                                                           SearchParams p,
+                                                                                           const uint2 *dbp) {
+    constexpr int SMEM = kSmemStackDefault;
+    __shared__ uint32_t s_bases[kReadWords * kThreads];
+    __shared__ uint32_t s_nmask[kMaskWords * kThreads];
+    __shared__ uint4 s_stack[SMEM * kThreads];
+    const HeavyCtx H = p.heavy;
+    uint32_t *sb = s_bases + threadIdx.x, *sn = s_nmask + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u, warp_col = threadIdx.x & ~31u;
+    const unsigned FULL = 0xFFFFFFFFu;
+    uint4 stk[STACK_CAP - SMEM], cand[kCandCap];
+    FlatLane<STACK_CAP, SMEM> L;
+    L.sstk = s_stack + threadIdx.x;
+    L.stk = stk;
+    L.cand = cand;
+    L.has_next = false;
+    L.phase = PH_IDLE;
+    L.r = 0;
+    L.sp = 0;
+    L.base = 0;
+    L.K = X.kmer_k;
+    L.role = ROLE_OWN;
+    L.owner = lane;
+    L.outstanding = 0;
+    L.heavy_seen = false;
+    L.nc = 0;
+    L.flags = 0;
+    L.own_rv = ReadView{sb, sn};
+    L.rv = L.own_rv;
+    uint32_t hid = 0;
+    const uint32_t n_heavy = min(vload(&H.hdr->n_heavy), kHeavyReads);
+    if (n_heavy == 0) return;
+    const uint32_t low_water = 2u * gridDim.x * kThreads;  // ring entries kept available
+    uint32_t idle_trips = 0;  // consecutive trips with no lane of the warp at work (warp-uniform)
+    for (unsigned long long it = 0;; it++) {
+        if (it >= p.loop_limit || idle_trips >= (1u << 23)) {  // guard: unfinished tasks mark their reads, the warp stops
+            if (lane == 0 && p.status) atomicOr(p.status, ALN_STATUS_LOOP_LIMIT);
+            if (L.role == ROLE_OWN && L.phase != PH_IDLE && L.phase != PH_FREE)
+                atomicOr(&H.reads[hid].flags, ALN_FLAG_LOOP_LIMIT);
+            break;
+        }
+        FetchReq fr;
+        fr.kind = F_NONE;
+        // control: advance the lane's task until it needs four extensions
+        for (int round = 0; round < 32; round++) {
+            if (L.phase == PH_FREE || L.phase == PH_RETURN || L.phase == PH_IDLE) break;
+            if (L.phase == PH_WAIT) {
+                if (L.outstanding) break;
+                L.phase = PH_DFS;
+            }
+            if (!L.has_next && L.sp == L.base) {
+                L.sp = L.base = 0;
+                if (L.role == ROLE_HELP) {
+                    L.phase = PH_RETURN;
+                    L.ret_i = 0;
+                    break;
+                }
+                if (L.outstanding) {
+                    L.phase = PH_WAIT;
+                    break;
+                }
+                // task done: its candidates into the read's table, then the next task
+                uint32_t f = L.flags & ALN_FLAG_INCOMPLETE;
+                for (uint32_t j = 0; j < L.nc; j++) {
+                    const uint4 c = L.cand[j];
+                    if (!heavy_insert(H, hid, c.z >> 31, c.x, c.y, c.z)) f |= ALN_FLAG_CAND_OVERFLOW;
+                }
+                if (f) atomicOr(&H.reads[hid].flags, f);
+                atomicSub(&H.hdr->outstanding, 1u);
+                L.phase = PH_IDLE;
+                break;
+            }
+            if (++L.work > p.work_limit) {
+                L.flags |= ALN_FLAG_WORK_LIMIT;
+                L.sp = L.base;
+                L.has_next = false;
+                continue;
+            }
+            if (L.expand_top(p, fr)) break;
+        }
+        __syncwarp();
+        if (fr.kind != F_NONE) {
+            uint32_t lo4[4], hi4[4];
+            fetch4(X, fr, lo4, hi4);
+            L.apply(X, lo4, hi4);
+        }
+        // the ring runs low: a task owner gives its bottom stack entry back to it
+        if (L.role == ROLE_OWN && L.phase == PH_DFS && (L.sp - L.base >= 2 || (L.sp - L.base >= 1 && L.has_next)) &&
+            vload(&H.hdr->tail) - vload(&H.hdr->head) < low_water) {
+            const uint4 e = L.stk_get(L.base);
+            L.base++;
+            heavy_push(H, e, hid, L.s);
+        }
+        L.exchange(lane, s_bases, s_nmask, warp_col, 0u);
+        // idle lanes take tasks from the ring, one claim per warp
+        const unsigned idle = __ballot_sync(FULL, L.phase == PH_IDLE);
+        if (idle) {
+            const uint32_t leader = __ffs(idle) - 1;
+            uint32_t first = 0, got = 0;
+            if (lane == leader) {
+                const uint32_t want = __popc(idle);
+                uint32_t h = vload(&H.hdr->head);
+                for (int tries = 0; tries < 64; tries++) {
+                    const uint32_t t = vload(&H.hdr->tail);
+                    const int avail = static_cast<int>(t - h);
+                    if (avail <= 0) break;
+                    const uint32_t g = min(want, static_cast<uint32_t>(avail));
+                    const uint32_t old = atomicCAS(&H.hdr->head, h, h + g);
+                    if (old == h) {
+                        first = h;
+                        got = g;
+                        break;
+                    }
+                    h = old;
+                }
+            }
+            first = __shfl_sync(FULL, first, leader);
+            got = __shfl_sync(FULL, got, leader);
+            const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
+            if (L.phase == PH_IDLE) {
+                if (rank < got) {
+                    const uint32_t t = first + rank;
+                    uint32_t spins = 0;
+                    while (vload(&H.ready[t % kHeavyPool]) != t + 1u && spins < (1u << 22)) spins++;
+                    if (spins >= (1u << 22)) {  // a published task that never appeared: give up
+                        if (p.status) atomicOr(p.status, ALN_STATUS_LOOP_LIMIT);
+                        L.phase = PH_FREE;
+                    } else {
+                        __threadfence();  // the task's slot was written before its ready word
+                        const HeavyTask *slot = H.pool + (t % kHeavyPool);
+                        HeavyTask task;
+                        task.node = __ldcg(&slot->node);
+                        task.hid = __ldcg(&slot->hid);
+                        task.s = __ldcg(&slot->s);
+                        hid = task.hid;
+                        const HeavyRead R = H.reads[hid];
+                        L.r = R.r;
+                        L.m = R.m;
+                        L.z = R.z;
+                        L.B = R.B;
+                        L.s = task.s;
+                        load_read(rb, rb.offset[R.r], R.m, sb, sn);
+                        const uint2 bp = dbp[2ull * R.r + task.s];
+                        if (task.s) {
+                            L.bpb0 = bp.x;
+                            L.bpb1 = bp.y;
+                        } else {
+                            L.bpa0 = bp.x;
+                            L.bpa1 = bp.y;
+                        }
+                        L.rv = L.own_rv;
+                        L.role = ROLE_OWN;
+                        L.next = task.node;
+                        L.has_next = true;
+                        L.sp = L.base = 0;
+                        L.nc = 0;
+                        L.work = 0;
+                        L.flags = 0;
+                        L.outstanding = 0;
+                        L.phase = PH_DFS;
+                    }
+                } else if (got == 0 && vload(&H.hdr->outstanding) == 0) {
+                    L.phase = PH_FREE;  // the pass is over
+                }
+            }
+            if (__ballot_sync(FULL, L.phase != PH_IDLE && L.phase != PH_FREE) == 0) {
+                __nanosleep(500);
+                idle_trips++;  // about 4 s of trips with nothing to do ends the warp (a task that never came)
+            } else {
+                idle_trips = 0;
+            }
+        } else {
+            idle_trips = 0;
+        }
+        if (__ballot_sync(FULL, L.phase != PH_FREE) == 0) break;
+    }
+}
+
+// One block per handed-over read after a pass: the iterative deepening rule on
+// its table; the result, or the next pass's budget, cleared tables and roots.
+__global__ void aln_heavy_decide_kernel(SearchParams p, const uint2 *dbp, uint32_t n_text, aln_read_result *res,
+                                        aln_hit *hits, int last) {
+    const HeavyCtx H = p.heavy;
+    const uint32_t hid = blockIdx.x;
+    if (hid >= min(H.hdr->n_heavy, kHeavyReads)) return;
+    HeavyRead *R = H.reads + hid;
+    if (R->state != 0) return;
+    HeavySlot *T = H.slots + static_cast<uint64_t>(hid) * 2 * kHeavySlots;
+    __shared__ uint32_t s_dmin, s_n;
+    __shared__ uint32_t s_next;  // 0 finish, else the next pass budget
+    __shared__ uint32_t s_final;
+    if (threadIdx.x == 0) {
+        s_dmin = 255;
+        s_n = 0;
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < 2 * kHeavySlots; j += blockDim.x)
+        if (T[j].id) {
+            atomicMin(&s_dmin, (T[j].key >> 28) & 7u);
+            atomicAdd(&s_n, 1u);
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t z = R->z, B = R->B;
+        uint32_t next = 0, fin = 0;
+        if (s_n > static_cast<uint32_t>(kCandCap)) R->flags |= ALN_FLAG_CAND_OVERFLOW;
+        if ((R->flags & ALN_FLAG_INCOMPLETE) || p.strata == ALN_STRATA_FULL) {
+            fin = z;
+        } else if (s_n == 0) {
+            if (B < z) next = min(z, B + 2);
+            fin = 0;
+        } else {
+            const uint32_t F = min(z, s_dmin + 1);
+            if (F <= B) fin = F;
+            else next = F;
+        }
+        if (next && last) {  // cannot happen within kHeavyPasses passes; leave no read without a result
+            R->flags |= ALN_FLAG_LOOP_LIMIT;
+            next = 0;
+            fin = B;
+        }
+        s_next = next;
+        s_final = fin;
+    }
+    __syncthreads();
+    if (s_next) {  // next pass: clear the tables, then the roots
+        for (uint32_t j = threadIdx.x; j < 2 * kHeavySlots; j += blockDim.x) {
+            T[j].id = 0ull;
+            T[j].key = 0xFFFFFFFFu;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            R->B = s_next;
+            R->distinct[0] = R->distinct[1] = 0;
+            const uint2 a = dbp[2ull * R->r], b = dbp[2ull * R->r + 1];
+            const uint4 root = make_uint4(0, n_text + 1, pack_info(0, 0, 0, 0, 0, 0, OP_M), 0);
+            if (d_at(a.x, a.y, 0) <= s_next) heavy_push(H, root, hid, 0);
+            if (d_at(b.x, b.y, 0) <= s_next) heavy_push(H, root, hid, 1);
+        }
+        return;
+    }
+    if (threadIdx.x != 0) return;
+    // the result: hits with diffs <= the final budget, ordered (diffs, strand, k, l)
+    const uint32_t fin = s_final;
+    aln_read_result out;
+    out.c0 = out.c1 = 0;
+    out.n_hits = 0;
+    out.d_best = 255;
+    out.reserved = 0;
+    uint32_t dbest = 255;
+    for (uint32_t j = 0; j < 2 * kHeavySlots; j++)
+        if (T[j].id && ((T[j].key >> 28) & 7u) <= fin) dbest = min(dbest, (T[j].key >> 28) & 7u);
+    uint32_t flags = R->flags & 0xFFu;
+    if (dbest != 255 && s_n) {
+        unsigned long long c0 = 0, c1 = 0;
+        uint32_t kept = 0;
+        for (uint32_t j = 0; j < 2 * kHeavySlots; j++) {
+            if (!T[j].id) continue;
+            const uint32_t d = (T[j].key >> 28) & 7u;
+            if (d > fin) continue;
+            kept++;
+            const unsigned long long w = (T[j].id & 0xFFFFFFFFull) - (T[j].id >> 32);
+            if (d == dbest) c0 += w;
+            else if (d == dbest + 1) c1 += w;
+        }
+        out.c0 = c0 > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(c0);
+        out.c1 = c1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(c1);
+        out.d_best = static_cast<uint8_t>(dbest);
+        const uint32_t nout = min(kept, p.hit_cap);
+        if (kept > p.hit_cap) flags |= ALN_FLAG_HIT_OVERFLOW;
+        aln_hit *Hh = hits + static_cast<uint64_t>(R->r) * p.hit_cap;
+        // selection of the nout smallest by (diffs, strand, k, l): each round takes
+        // the least entry above the previous one
+        uint32_t pk = 0, pl = 0, pkey = 0;
+        bool have_prev = false;
+        for (uint32_t t = 0; t < nout; t++) {
+            bool found = false;
+            uint32_t bk = 0, bl = 0, bkey = 0;
+            for (uint32_t j = 0; j < 2 * kHeavySlots; j++) {
+                if (!T[j].id) continue;
+                const uint32_t key = T[j].key;
+                const uint32_t d = (key >> 28) & 7u;
+                if (d > fin) continue;
+                const uint32_t k = static_cast<uint32_t>(T[j].id >> 32), l = static_cast<uint32_t>(T[j].id);
+                const uint32_t o = (d << 1) | (key >> 31);
+                if (have_prev) {
+                    const uint32_t po = (((pkey >> 28) & 7u) << 1) | (pkey >> 31);
+                    if (o < po || (o == po && (k < pk || (k == pk && l <= pl)))) continue;
+                }
+                if (!found) {
+                    found = true;
+                    bk = k; bl = l; bkey = key;
+                } else {
+                    const uint32_t bo = (((bkey >> 28) & 7u) << 1) | (bkey >> 31);
+                    if (o < bo || (o == bo && (k < bk || (k == bk && l < bl)))) {
+                        bk = k; bl = l; bkey = key;
+                    }
+                }
+            }
+            aln_hit h;
+            h.k = bk;
+            h.l = bl - 1;
+            h.aligned_len = static_cast<uint16_t>(bkey & 0xFFFFu);
+            h.strand = static_cast<uint8_t>(bkey >> 31);
+            h.n_diff = static_cast<uint8_t>((bkey >> 28) & 7u);
+            h.n_gapo = static_cast<uint8_t>((bkey >> 24) & 15u);
+            h.n_gape = static_cast<uint8_t>((bkey >> 20) & 15u);
+            h.n_mm = static_cast<uint8_t>((bkey >> 16) & 15u);
+            h.reserved = 0;
+            Hh[t] = h;
+            pk = bk; pl = bl; pkey = bkey;
+            have_prev = true;
+        }
+        out.n_hits = static_cast<uint8_t>(nout);
+    }
+    out.flags = static_cast<uint8_t>(flags);
+    res[R->r] = out;
+    R->state = 1;
+}
+
 #ifdef ALN_STATS
 cudaError_t debug_stats(unsigned long long *out, int reset) {
     cudaError_t e = cudaMemcpyFromSymbol(out, g_stats, sizeof(g_stats));
@@ -231,6 +633,7 @@ __global__ void aln_order_scatter_kernel(const uint2 *dbp, uint32_t n, const uin
 }
 
 int stack_cap_for(uint32_t z) { return z <= 2 ? 19 : (z <= 4 ? 37 : 64); }
+HeavyCtx heavy_layout(void *scratch, uint32_t n);
 
 template <int CAP, int SMEM>
 static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
@@ -252,10 +655,17 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
         cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
         uint2 *dbp = nullptr;
         uint32_t *order = nullptr;
+        SearchParams pp = p;
+        pp.heavy.hdr = nullptr;
         if (scratch) {  // D pre-pass and visit order (layout: search_scratch_bytes)
             uint32_t *counts = static_cast<uint32_t *>(scratch), *cursor = counts + kOrderBins;
             dbp = reinterpret_cast<uint2 *>(static_cast<char *>(scratch) + 256);
             order = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + 256 + 16ull * n);
+            if (p.heavy_after != 0xFFFFFFFFu) {  // the heavy phase's state after them
+                pp.heavy = heavy_layout(scratch, n);
+                cudaMemsetAsync(pp.heavy.hdr, 0, sizeof(HeavyHdr), st);
+                cudaMemsetAsync(pp.heavy.ready, 0, 4ull * kHeavyPool, st);
+            }
             cudaMemsetAsync(scratch, 0, 2 * kOrderBins * sizeof(uint32_t), st);
             aln_dscan_kernel<<<static_cast<unsigned>((2ull * n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
                 X, rb, n, p, dbp);
@@ -263,7 +673,39 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
             aln_order_count_kernel<<<ob, 256, 0, st>>>(dbp, n, counts);
             aln_order_scatter_kernel<<<ob, 256, 0, st>>>(dbp, n, counts, cursor, order);
         }
-        aln_persistent_kernel<CAP, SMEM><<<blocks, kThreads, 0, st>>>(X, rb, n, p, res, hits, queue, order, dbp);
+        const SearchParams &p1 = pp;
+        if (p.window_base && p.window_bytes) {  // prefix-trie tables held in L2's persisting set
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(blocks);
+            cfg.blockDim = dim3(kThreads);
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+            attr[0].val.accessPolicyWindow.base_ptr = p.window_base;
+            attr[0].val.accessPolicyWindow.num_bytes = p.window_bytes;
+            attr[0].val.accessPolicyWindow.hitRatio = p.window_hit_ratio;
+            attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+            attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const cudaError_t e = cudaLaunchKernelEx(&cfg, aln_persistent_kernel<CAP, SMEM>, X, rb, n, p1, res, hits,
+                                                     queue, static_cast<const uint32_t *>(order),
+                                                     static_cast<const uint2 *>(dbp));
+            if (e != cudaSuccess) return e;
+        } else {
+            aln_persistent_kernel<CAP, SMEM><<<blocks, kThreads, 0, st>>>(X, rb, n, p1, res, hits, queue, order, dbp);
+        }
+        if (pp.heavy.hdr) {  // the reads handed over, one deepening pass per launch over the whole GPU
+            int hb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hb, aln_heavy_pass_kernel<CAP>, kThreads, 0);
+            const unsigned hgrid = static_cast<unsigned>(sms * (hb > 0 ? hb : 1));
+            aln_heavy_start_kernel<<<kHeavyReads, 128, 0, st>>>(pp, dbp, X.t[0].n);
+            for (uint32_t pass = 0; pass < kHeavyPasses; pass++) {
+                aln_heavy_pass_kernel<CAP><<<hgrid, kThreads, 0, st>>>(X, rb, pp, dbp);
+                aln_heavy_decide_kernel<<<kHeavyReads, 128, 0, st>>>(pp, dbp, X.t[0].n, res, hits,
+                                                                    pass + 1 == kHeavyPasses ? 1 : 0);
+            }
+        }
     }
     return cudaGetLastError();
 }
@@ -293,8 +735,29 @@ int persistent_max_blocks(uint32_t z, uint32_t smem) {
 bool smem_stack_supported(uint32_t smem) { return smem == 0 || smem == 4 || smem == 8 || smem == 12; }
 
 // Bytes of the optional persistent-mode scratch for n reads: order-sort counters
-// (256 B), D breakpoints (2 x 8 B per read), visit order (4 B per read).
-uint64_t search_scratch_bytes(uint32_t n) { return 256ull + 20ull * n; }
+// (256 B), D breakpoints (2 x 8 B per read), visit order (4 B per read), then
+// from the next 256-byte boundary the heavy phase: its header, the handed-over
+// reads, their candidate tables, the task ring and its ready words.
+static uint64_t heavy_offset(uint32_t n) { return (256ull + 20ull * n + 255ull) & ~255ull; }
+static constexpr uint64_t kHeavyBytes = sizeof(HeavyHdr) + kHeavyReads * sizeof(HeavyRead) +
+                                        2ull * kHeavyReads * kHeavySlots * sizeof(HeavySlot) +
+                                        kHeavyPool * sizeof(HeavyTask) + 4ull * kHeavyPool;
+uint64_t search_scratch_bytes(uint32_t n) { return heavy_offset(n) + kHeavyBytes; }
+
+HeavyCtx heavy_layout(void *scratch, uint32_t n) {
+    char *b = static_cast<char *>(scratch) + heavy_offset(n);
+    HeavyCtx H;
+    H.hdr = reinterpret_cast<HeavyHdr *>(b);
+    b += sizeof(HeavyHdr);
+    H.reads = reinterpret_cast<HeavyRead *>(b);
+    b += kHeavyReads * sizeof(HeavyRead);
+    H.slots = reinterpret_cast<HeavySlot *>(b);
+    b += 2ull * kHeavyReads * kHeavySlots * sizeof(HeavySlot);
+    H.pool = reinterpret_cast<HeavyTask *>(b);
+    b += kHeavyPool * sizeof(HeavyTask);
+    H.ready = reinterpret_cast<uint32_t *>(b);
+    return H;
+}
 
 template <int CAP>
 static cudaError_t launch_smem(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,

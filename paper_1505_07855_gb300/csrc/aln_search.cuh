@@ -34,7 +34,8 @@ constexpr int kReadWords = 16;  // 2-bit words for ALN_MAX_READ_LEN bases
 constexpr int kMaskWords = 8;   // N-mask words
 constexpr int kCandCap = ALN_CAND_CAP;
 constexpr uint32_t kDefaultWorkLimit = 1u << 24;
-constexpr uint32_t kDefaultHelpAfter = 4096;
+constexpr uint32_t kDefaultHelpAfter = 0xFFFFFFFFu;  // only once the read queue is empty
+constexpr uint32_t kDefaultHeavyAfter = 1u << 18;
 
 enum : uint32_t { OP_M = 0, OP_I = 1, OP_D = 2 };
 
@@ -46,12 +47,53 @@ struct ReadBatch {
     const uint8_t *z;
 };
 
+// Heavy-read phase (device-wide search of the reads that passed heavy_after
+// expansions in the persistent search): its state lives in the call's scratch.
+constexpr uint32_t kHeavyReads = 2048;     // reads the heavy phase takes per call
+constexpr uint32_t kHeavySlots = 1024;     // candidate hash slots per read and strand
+constexpr uint32_t kHeavyPool = 1u << 20;  // task ring capacity
+constexpr uint32_t kHeavyPasses = 5;       // deepening passes launched (enough for z <= 7)
+
+struct HeavyHdr {   // 256 bytes
+    uint32_t n_heavy;      // reads handed over (may pass kHeavyReads: those stay in the first phase)
+    uint32_t head, tail;   // task ring tickets: taken, published
+    uint32_t outstanding;  // tasks of the current pass not yet finished
+    uint32_t pad[60];
+};
+struct HeavyRead {  // 64 bytes
+    uint32_t r, B, z, m;   // read index, pass budget, difference limit, length
+    uint32_t state;        // 0 searching, 1 result written
+    uint32_t flags;        // ALN_FLAG_* gathered from the tasks
+    uint32_t distinct[2];  // distinct candidates per strand in this pass
+    uint32_t pad[8];
+};
+struct HeavyTask {  // 32 bytes
+    uint4 node;
+    uint32_t hid, s, pad0, pad1;
+};
+struct HeavySlot {  // 16 bytes: a candidate (lo, hi) of one strand with its least witness key
+    unsigned long long id;  // lo << 32 | hi; 0 = empty
+    uint32_t key, pad;
+};
+struct HeavyCtx {
+    HeavyHdr *hdr;
+    HeavyRead *reads;
+    HeavySlot *slots;      // [hid][strand][kHeavySlots]
+    HeavyTask *pool;
+    uint32_t *ready;       // ready[t % kHeavyPool] = t + 1 once task t is written
+};
+
 struct SearchParams {
     uint32_t z, max_gapo, max_gape, seed_len, seed_z, e, hit_cap, strata, work_limit, blocks_per_sm;
     uint32_t smem_stack;            // persistent form: stack entries per lane in shared memory
     uint32_t help_after;            // persistent form: expansions after which a read takes idle lanes
+    uint32_t heavy_after;           // persistent form: owner expansions after which a read goes to the heavy phase
+    HeavyCtx heavy;                 // heavy phase state (hdr == nullptr: no heavy phase)
     unsigned long long loop_limit;  // persistent form: loop trips per warp
     uint32_t *status;               // ALN_STATUS_* bits, or nullptr
+    void *window_base;              // persistent form: L2 persisting window (prefix-trie tables), or nullptr
+    uint64_t window_bytes;
+    float window_hit_ratio;
 };
 
 // Stack-entry info word: i (8) | n_mm (3) | n_gapo (3) | n_gape (3) | n_ins (3) | seed (3) | last (2)

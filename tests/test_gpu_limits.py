@@ -115,3 +115,32 @@ def test_two_captured_searches_replay_side_by_side(setup):
         h = hits.cpu().numpy().view(aln.HIT_DTYPE)[:m * 16].reshape(m, 16)
         compare(r, h, ro[idx], ho[idx], idx=idx, what="side-by-side replay")
     assert HIT_FIELDS
+
+
+def test_compact_hits_equals_host_compaction(setup):
+    """aln_compact_hits: per-read offsets and the written hits back to back, equal
+    to compacting the per-read slots on the host; with a dense array too small
+    the total is still reported and only the hits that fit are written."""
+    torch, w, ox, al, ro, ho = setup
+    n, cap = w.reads.n, 16
+    p = aln.Params.from_limits(w.params, hit_cap=cap, mode=aln.MODE_PERSISTENT)
+    d = al.upload(w.reads.codes, w.reads.offsets, w.reads.lens)
+    res, hits = al.outputs(n, cap)
+    al.search_device(d, p, res, hits)
+    r = res.cpu().numpy().view(aln.RES_DTYPE)[:n]
+    h = hits.cpu().numpy().view(aln.HIT_DTYPE)[:n * cap].reshape(n, cap)
+    exp = h[np.arange(cap)[None, :] < r["n_hits"][:, None]]
+    exp_off = np.concatenate([[0], np.cumsum(r["n_hits"].astype(np.int64))])
+    scratch = al.compact_scratch(n)
+    for room in (exp.size + 7, exp.size // 2):
+        offsets = torch.zeros(n + 1, dtype=torch.int32, device=al.dev)
+        dense = torch.full((max(1, room) * aln.HIT_DTYPE.itemsize,), 0xEE, dtype=torch.uint8, device=al.dev)
+        al.compact(res, hits, n, cap, offsets, dense, scratch)
+        torch.cuda.synchronize()
+        off = offsets.cpu().numpy().view(np.uint32)
+        dd = dense.cpu().numpy().view(aln.HIT_DTYPE)
+        assert np.array_equal(off.astype(np.int64), exp_off)
+        k = min(room, exp.size)
+        assert dd[:k].tobytes() == exp[:k].tobytes()
+        if room > exp.size:
+            assert (dense.cpu().numpy()[exp.size * 16:] == 0xEE).all()

@@ -121,11 +121,34 @@ def test_mixed_lengths_per_read_z(cuda):
         compare(rg, hg, ro, ho, what=f"mixed mode {mode} kmer {k}")
     # schedule knobs are result-neutral: heavy reads helped at once or only at the
     # end, every shared-memory stack depth, few resident blocks
-    for help_after, smem, bps in [(1, 4, 0), (0xFFFFFFFF, 12, 0), (64, 8, 1), (0, 12, 2)]:
+    for help_after, smem, bps, win, heavy in [(1, 4, 0, 0, 0), (0xFFFFFFFF, 12, 0, 1, 1), (64, 8, 1, 0, 64),
+                                              (0, 12, 2, 1, 0xFFFFFFFF)]:
         p = aln.Params.from_limits(lim, hit_cap=32, mode=aln.MODE_PERSISTENT, z=6, help_after=help_after,
-                                   smem_stack=smem, blocks_per_sm=bps)
+                                   smem_stack=smem, blocks_per_sm=bps, l2_window=win, heavy_after=heavy)
         rg, hg = pair.als[11].align(w.reads.codes, w.reads.offsets, w.reads.lens, p, z=w.reads.z)
-        compare(rg, hg, ro, ho, what=f"mixed help_after {help_after} smem {smem} blocks {bps}")
+        compare(rg, hg, ro, ho, what=f"mixed help_after {help_after} smem {smem} blocks {bps} l2 window {win} "
+                                     f"heavy_after {heavy}")
+
+
+@pytest.mark.parametrize("li", [1, 4, 6])
+@pytest.mark.parametrize("strata", [aln.STRATA_BEST1, aln.STRATA_FULL])
+def test_heavy_phase_parity(cuda, li, strata):
+    """The heavy phase (reads handed to a search by every lane of the GPU) gives
+    the oracle's results: with heavy_after = 1 almost every read of the batch is
+    handed over (2048 per call; the rest stay with their warps), across gap,
+    seed and z settings and both strata."""
+    lim = LIMITS[li]
+    rng = Rng(3000 + li, "heavy")
+    text = reference_iid(30_000, rng.sub("t"))
+    pair = Pair(text, kmers=[0, 6])
+    m = [20, 36, 50, 36, 60, 76, 40][li]
+    reads = simulate_reads(text, 2500, m, rng.sub("r"), sub_rate=(0.02, 0.04), indel_rate=0.005,
+                           indel_lens=(1, 2), n_frac=0.1, z=lim["z"])
+    ro, ho, _ = oracle_align(pair.ox, reads, lim, 40, strata)
+    for k in (0, 6):
+        p = aln.Params.from_limits(lim, hit_cap=40, strata=strata, mode=aln.MODE_PERSISTENT, heavy_after=1)
+        rg, hg = pair.als[k].align(reads.codes, reads.offsets, reads.lens, p)
+        compare(rg, hg, ro, ho, what=f"heavy limits {li} kmer {k}")
 
 
 def _positions_parity(pair, rg, hg, what):
@@ -159,6 +182,34 @@ def test_pairs_recipe_parity(cuda):
         compare(rg, hg, ro, ho, what=f"pairs mode {mode} kmer {k}")
     assert (rg["n_hits"] > 0).mean() > 0.95
     assert _positions_parity(pair, rg, hg, "pairs positions") > 5000
+
+
+def test_pairing_parity(cuda):
+    """The pairing stage on the GPU (compaction, SA walk, aln_pair_resolve) against
+    the oracle's pairing of its own search results: every field of every pair and
+    the insert-size window, on the paired-end recipe at 3 Mbp (N runs, repeats,
+    chimeric pairs) with two placement caps."""
+    w = workload("human_pairs", ref_len=3_000_000, n_reads=5000, seed=8)
+    pair = Pair(w.text, kmers=[BENCH_KMER])
+    al = pair.al
+    cap = 32
+    p = aln.Params.from_limits(w.params, hit_cap=cap, mode=aln.MODE_PERSISTENT)
+    d = al.upload(w.reads.codes, w.reads.offsets, w.reads.lens)
+    res, hits = al.outputs(d["n"], cap)
+    al.search_device(d, p, res, hits)
+    ro, ho, _ = oracle_align(pair.ox, w.reads, w.params, cap, oracle.BEST1)
+    rg = res.cpu().numpy().view(aln.RES_DTYPE)[:d["n"]]
+    hg = hits.cpu().numpy().view(aln.HIT_DTYPE)[:d["n"] * cap].reshape(d["n"], cap)
+    compare(rg, hg, ro, ho, what="pairing input")
+    for max_place in (16, 4):
+        gp, gst = al.pair(res, d["n"], cap, hits, 16, max_place)
+        op, ost = pair.ox.pair_resolve(ro, ho, max_place)
+        assert gst == ost, (gst, ost)
+        for f in ("pos", "insert", "n_proper", "strand", "flags"):
+            bad = np.nonzero((gp[f] != op[f]).reshape(gp.size, -1).any(axis=1))[0]
+            assert bad.size == 0, f"max_place {max_place}: {f} differs at pair {bad[0]}: {gp[bad[0]]} vs {op[bad[0]]}"
+        assert ((gp["flags"] & aln.PAIR_PROPER) != 0).mean() > 0.9
+    assert gst["n_unique"] > 3000 and abs(gst["q2"] - 500) <= 10
 
 
 def test_chr100_scaled_parity(cuda):
