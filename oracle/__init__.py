@@ -33,12 +33,14 @@ PAIR_UNIQUE, PAIR_PROPER, PAIR_DISCORDANT = 0x10, 0x20, 0x40
 FLAG_HIT_OVERFLOW = 0x01
 FLAG_READ_TOO_LONG = 0x08
 FLAG_BAD_LIMIT = 0x10
-BEST1, FULL = 0, 1
+FLAG_MANY_BEST = 0x80
+BEST1, FULL, SCORE = 0, 1, 2
 
 
 class _Params(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int) for f in ("z", "max_gapo", "max_gape", "seed_len", "seed_z",
-                                            "indel_end_skip", "hit_cap", "strata", "use_d")]
+                                            "indel_end_skip", "hit_cap", "strata", "use_d",
+                                            "sc_mm", "sc_gapo", "sc_gape", "max_best")]
 
 
 def build(force: bool = False) -> str:
@@ -163,9 +165,10 @@ class OracleIndex:
 
     def align(self, codes, offsets, lens, z=None, *, z_default=2, max_gapo=1, max_gape=2,
               seed_len=0, seed_z=0, indel_end_skip=5, hit_cap=32, strata=BEST1, use_d=True,
-              threads: int | None = None):
+              threads: int | None = None, score=(3, 11, 4), max_best=0):
         """Search a batch.  Returns (res[n] RES_DTYPE, hits[n, hit_cap] HIT_DTYPE,
-        lookups[n] uint64)."""
+        lookups[n] uint64).  strata SCORE: hits ranked by the penalties `score`
+        (mismatch, gap open, gap extension); res["pad"] holds the best score."""
         codes = np.ascontiguousarray(codes, dtype=np.uint8)
         offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
         lens = np.ascontiguousarray(lens, dtype=np.uint16)
@@ -175,7 +178,7 @@ class OracleIndex:
             z = np.ascontiguousarray(z, dtype=np.uint8)
             zp = _ptr(z)
         p = _Params(z_default, max_gapo, max_gape, seed_len, seed_z, indel_end_skip, hit_cap,
-                    strata, 1 if use_d else 0)
+                    strata, 1 if use_d else 0, score[0], score[1], score[2], max_best)
         res = np.zeros(n, RES_DTYPE)
         hits = np.zeros((n, max(1, hit_cap)), HIT_DTYPE)
         look = np.zeros(n, np.uint64)

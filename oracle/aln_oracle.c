@@ -46,6 +46,8 @@
 #define F_HIT_OVERFLOW 0x01
 #define F_READ_TOO_LONG 0x08
 #define F_BAD_LIMIT 0x10
+#define F_MANY_BEST 0x80
+#define STRATA_SCORE 2    /* score-ordered mode: see align_one */
 
 typedef struct {
     uint64_t n;        /* text length without $ */
@@ -348,6 +350,8 @@ typedef struct {
     int hit_cap;
     int strata;          /* 0 = BEST1, 1 = FULL */
     int use_d;           /* 1 = prune with D, 0 = D taken as all zero */
+    int sc_mm, sc_gapo, sc_gape; /* score-ordered mode: penalty of a mismatch, gap open, gap extension */
+    int max_best;        /* score-ordered mode: more best placements than this list the best only; 0 = no cap */
 } orc_params;
 
 typedef struct {         /* one reported hit */
@@ -378,8 +382,20 @@ typedef struct {
 enum { OP_M = 0, OP_I = 1, OP_D = 2 };
 
 /* witness order: (diffs, n_gapo, n_gape, n_mm, aligned_len) */
-static int witness_less(const orc_hit *a, const orc_hit *b)
+/* Penalty score of a witness (score-ordered mode): lower is better. */
+static int score_of(const orc_params *p, const orc_hit *h)
 {
+    return p->sc_mm * h->n_mm + p->sc_gapo * h->n_gapo + p->sc_gape * h->n_gape;
+}
+
+/* witness order: (diffs, n_gapo, n_gape, n_mm, aligned_len), in the
+ * score-ordered mode preceded by the score */
+static int witness_less(const orc_hit *a, const orc_hit *b, const orc_params *p)
+{
+    if (p->strata == STRATA_SCORE) {
+        int sa = score_of(p, a), sb = score_of(p, b);
+        if (sa != sb) return sa < sb;
+    }
     if (a->n_diff != b->n_diff) return a->n_diff < b->n_diff;
     if (a->n_gapo != b->n_gapo) return a->n_gapo < b->n_gapo;
     if (a->n_gape != b->n_gape) return a->n_gape < b->n_gape;
@@ -398,7 +414,7 @@ static void record(ctx_t *c, uint64_t k, uint64_t l, int n_mm, int n_gapo, int n
     for (int i = 0; i < c->n_cand; i++) {
         orc_hit *o = &c->cand[i];
         if (o->strand == h.strand && o->k == h.k && o->l == h.l) {
-            if (witness_less(&h, o)) *o = h;
+            if (witness_less(&h, o, c->p)) *o = h;
             return;
         }
     }
@@ -544,6 +560,72 @@ static int search_pass(ctx_t c[2], int budget)
     return c[0].n_cand + c[1].n_cand;
 }
 
+/*
+ * Score-ordered mode (the variant BWA and BarraCUDA ship: hits ranked by a
+ * mismatch / gap-open / gap-extension penalty rather than by difference count).
+ * The hits are every hit within the difference limit z (as in FULL), each with
+ * its least witness by (score, diffs, gap opens, gap extensions, mismatches,
+ * length).  S1 = the least score, S2 = the least score above it; c0 / c1 = the
+ * summed widths of the hits scoring S1 / S2; the hits scoring S1 or S2 are
+ * listed in the order (score, strand, k, l), only those scoring S1 when more
+ * than max_best places score S1 (> 0; flag F_MANY_BEST).  d_best = the fewest
+ * differences among the S1 hits; the result's spare byte holds S1 (at most 254).
+ */
+static void score_strata(const orc_params *p, orc_hit *all, int nc, orc_res *res, orc_hit *hits)
+{
+    int s1 = -1, s2 = -1;
+    for (int i = 0; i < nc; i++) {
+        int sc = score_of(p, &all[i]);
+        if (s1 < 0 || sc < s1) s1 = sc;
+    }
+    for (int i = 0; i < nc; i++) {
+        int sc = score_of(p, &all[i]);
+        if (sc > s1 && (s2 < 0 || sc < s2)) s2 = sc;
+    }
+    uint64_t c0 = 0, c1 = 0;
+    int d_best = 255;
+    for (int i = 0; i < nc; i++) {
+        int sc = score_of(p, &all[i]);
+        uint64_t wdt = (uint64_t)all[i].l - all[i].k + 1;
+        if (sc == s1) {
+            c0 += wdt;
+            if (all[i].n_diff < d_best) d_best = all[i].n_diff;
+        } else if (sc == s2) {
+            c1 += wdt;
+        }
+    }
+    int many = p->max_best > 0 && c0 > (uint64_t)p->max_best;
+    int nk = 0;
+    for (int i = 0; i < nc; i++) {
+        int sc = score_of(p, &all[i]);
+        if (sc == s1 || (!many && sc == s2)) all[nk++] = all[i];
+    }
+    /* order (score, strand, k, l): insertion sort */
+    for (int i = 1; i < nk; i++) {
+        orc_hit h = all[i];
+        int sh = score_of(p, &h), j = i;
+        while (j > 0) {
+            const orc_hit *o = &all[j - 1];
+            int so = score_of(p, o);
+            int after = so > sh || (so == sh && (o->strand > h.strand || (o->strand == h.strand &&
+                        (o->k > h.k || (o->k == h.k && o->l > h.l)))));
+            if (!after) break;
+            all[j] = all[j - 1];
+            j--;
+        }
+        all[j] = h;
+    }
+    int out = nk < p->hit_cap ? nk : p->hit_cap;
+    if (nk > p->hit_cap) res->flags |= F_HIT_OVERFLOW;
+    if (many) res->flags |= F_MANY_BEST;
+    memcpy(hits, all, out * sizeof(orc_hit));
+    res->n_hits = (uint8_t)out;
+    res->d_best = (uint8_t)d_best;
+    res->pad = (uint8_t)(s1 > 254 ? 254 : s1);
+    res->c0 = c0 > 0xFFFFFFFFULL ? 0xFFFFFFFFu : (uint32_t)c0;
+    res->c1 = c1 > 0xFFFFFFFFULL ? 0xFFFFFFFFu : (uint32_t)c1;
+}
+
 /* Align one read; writes res and up to hit_cap hits; returns canonical lookups. */
 static uint64_t align_one(const orc_index *ix, const uint8_t *w, int m, int z, const orc_params *p,
                           orc_res *res, orc_hit *hits, ctx_t c[2])
@@ -562,7 +644,7 @@ static uint64_t align_one(const orc_index *ix, const uint8_t *w, int m, int z, c
         if (!p->use_d) for (int i = 0; i <= m; i++) c[s].D[i] = 0;
     }
     int final_budget = -1;
-    if (p->strata == 1) {
+    if (p->strata == 1 || p->strata == STRATA_SCORE) {
         final_budget = z;
         search_pass(c, z);
     } else {
@@ -583,6 +665,11 @@ static uint64_t align_one(const orc_index *ix, const uint8_t *w, int m, int z, c
     orc_hit *all = (orc_hit *)malloc(nc * sizeof(orc_hit));
     memcpy(all, c[0].cand, c[0].n_cand * sizeof(orc_hit));
     memcpy(all + c[0].n_cand, c[1].cand, c[1].n_cand * sizeof(orc_hit));
+    if (p->strata == STRATA_SCORE) {
+        score_strata(p, all, nc, res, hits);
+        free(all);
+        return look;
+    }
     int d_best = 255;
     for (int i = 0; i < nc; i++) if (all[i].n_diff < d_best) d_best = all[i].n_diff;
     int keep_max = (p->strata == 1) ? z : (d_best + 1 <= z ? d_best + 1 : z);

@@ -74,10 +74,14 @@ def _transcripts(Q, U, z, max_gapo, max_gape, seed_len, seed_z, e):
 
 
 def brute_hits(X: str, W: list[int], *, z, max_gapo, max_gape, seed_len=0, seed_z=0, e=5,
-               strata="FULL", hit_cap=255):
+               strata="FULL", hit_cap=255, score=(3, 11, 4), max_best=0):
     """Full result for one read by brute force.  Returns (hits, d_best, c0, c1, overflow)
     with hits as tuples (strand, k, l, n_diff, n_gapo, n_gape, n_mm, aligned_len) in
-    the order (diffs, strand, k, l)."""
+    the order (diffs, strand, k, l).  strata "SCORE" (hits ranked by the penalty
+    M n_mm + O n_gapo + E n_gape, score = (M, O, E)) returns (hits, d_best, c0,
+    c1, overflow, best_score, many_best) instead, hits in the order (score,
+    strand, k, l): the best and second-best scores listed, the best only when
+    more than max_best (> 0) places have the best score."""
     n = len(X)
     Xr = X[::-1]
     sa_x, sa_r = _sa_cached(X), _sa_cached(Xr)
@@ -101,9 +105,25 @@ def brute_hits(X: str, W: list[int], *, z, max_gapo, max_gape, seed_len=0, seed_
             assert iv is not None
             for (mm, go, ge) in tr:
                 w = (mm + go + ge, go, ge, mm, len(T))
+                if strata == "SCORE":
+                    w = (score[0] * mm + score[1] * go + score[2] * ge,) + w
                 key = (strand, iv[0], iv[1])
                 if key not in best or w < best[key]:
                     best[key] = w
+    if strata == "SCORE":
+        if not best:
+            return [], 255, 0, 0, False, 255, False
+        s1 = min(w[0] for w in best.values())
+        higher = [w[0] for w in best.values() if w[0] > s1]
+        s2 = min(higher) if higher else None
+        c0 = sum(l - k + 1 for (s, k, l), w in best.items() if w[0] == s1)
+        c1 = sum(l - k + 1 for (s, k, l), w in best.items() if w[0] == s2)
+        d_best = min(w[1] for w in best.values() if w[0] == s1)
+        many = max_best > 0 and c0 > max_best
+        kept = sorted((w[0], s, k, l, w) for (s, k, l), w in best.items()
+                      if w[0] == s1 or (not many and w[0] == s2))
+        hits = [(s, k, l, w[1], w[2], w[3], w[4], w[5]) for (_, s, k, l, w) in kept]
+        return hits[:hit_cap], d_best, c0, c1, len(hits) > hit_cap, min(s1, 254), many
     if not best:
         return [], 255, 0, 0, False
     d_best = min(w[0] for w in best.values())

@@ -39,6 +39,11 @@ MUTANTS = {
     "pair_same_strand_is_fr": ("*fr = a->strand != b->strand;", "*fr = 1;"),
     "pair_reverse_pos_no_len": ("out[k].pos = h[j].strand ? ix->t[0].sa[row] : n - ix->t[1].sa[row] - h[j].aligned_len;",
                                 "out[k].pos = h[j].strand ? ix->t[0].sa[row] : n - ix->t[1].sa[row];"),
+    "score_gapo_weight": ("return p->sc_mm * h->n_mm + p->sc_gapo * h->n_gapo + p->sc_gape * h->n_gape;",
+                          "return p->sc_mm * h->n_mm + p->sc_gape * h->n_gapo + p->sc_gape * h->n_gape;"),
+    "score_second_stratum": ("if (sc > s1 && (s2 < 0 || sc < s2)) s2 = sc;", "if (sc >= s1 && (s2 < 0 || sc < s2)) s2 = sc;"),
+    "score_many_best_inclusive": ("int many = p->max_best > 0 && c0 > (uint64_t)p->max_best;",
+                                  "int many = p->max_best > 0 && c0 >= (uint64_t)p->max_best;"),
     "dollar_largest": ("return li < lj ? -1 : (li > lj ? 1 : 0);", "return li > lj ? -1 : (li < lj ? 1 : 0);"),
     "best1_no_second_stratum": ("int keep_max = (p->strata == 1) ? z : (d_best + 1 <= z ? d_best + 1 : z);",
                                 "int keep_max = (p->strata == 1) ? z : d_best;"),
@@ -71,6 +76,8 @@ def _pin_calls():
         lambda: pins.test_every_position_every_edit(2),
         lambda: pins.test_against_brute_force(*c[2], "FULL"),
         lambda: pins.test_every_pair_of_edits_in_seed(1),
+        lambda: pins.test_score_mode_against_brute_force(0),
+        lambda: pins.test_score_mode_against_brute_force(2),
         pair_pins.test_pairing_hand_example,
         pair_pins.test_pairing_recovers_the_generated_fragments,
     ]

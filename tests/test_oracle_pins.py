@@ -255,6 +255,49 @@ def test_against_brute_force(n, m, lim, n_reads, seed, strata):
         assert (int(res[i]["c0"]), int(res[i]["c1"])) == (c0, c1)
 
 
+SCORE_CASES = [
+    (300, 16, dict(z=3, max_gapo=1, max_gape=1, seed_len=0, seed_z=0, e=2), 14, 51, (3, 11, 4), 0),
+    (250, 14, dict(z=3, max_gapo=2, max_gape=2, seed_len=0, seed_z=0, e=1), 14, 52, (1, 2, 1), 0),
+    (200, 12, dict(z=2, max_gapo=1, max_gape=1, seed_len=6, seed_z=1, e=1), 12, 56, (3, 11, 4), 1),
+    (120, 10, dict(z=2, max_gapo=1, max_gape=1, seed_len=0, seed_z=0, e=1), 12, 54, (2, 3, 1), 2),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SCORE_CASES)))
+def test_score_mode_against_brute_force(case):
+    """Score-ordered mode: hits with their least witness by penalty score, the
+    best and second-best score strata, c0 / c1, the best score, d_best and the
+    cap on equally best places, against the brute-force DP over every substring
+    (two-letter texts give many near-equal places, so the cap is exercised)."""
+    n, m, lim, n_reads, seed, score, max_best = SCORE_CASES[case]
+    t = _rand_text(n, seed, alphabet=4 if seed % 2 else 2)
+    X = codes_to_str(t)
+    ix = oracle.OracleIndex(t)
+    reads = _reads_from(t, n_reads, m, seed + 100, n_mut=2, with_n=True)
+    codes, offs, lens = _batch(reads)
+    res, hits, _ = ix.align(codes, offs, lens, z_default=lim["z"], max_gapo=lim["max_gapo"],
+                            max_gape=lim["max_gape"], seed_len=lim["seed_len"], seed_z=lim["seed_z"],
+                            indel_end_skip=lim["e"], hit_cap=255, strata=oracle.SCORE, score=score,
+                            max_best=max_best)
+    many_seen = 0
+    for i, w in enumerate(reads):
+        exp, d_best, c0, c1, _, s1, many = brute.brute_hits(
+            X, list(w), z=lim["z"], max_gapo=lim["max_gapo"], max_gape=lim["max_gape"],
+            seed_len=lim["seed_len"], seed_z=lim["seed_z"], e=lim["e"], strata="SCORE", score=score,
+            max_best=max_best)
+        got = [(int(h["strand"]), int(h["k"]), int(h["l"]), int(h["n_diff"]), int(h["n_gapo"]),
+                int(h["n_gape"]), int(h["n_mm"]), int(h["aligned_len"]))
+               for h in hits[i, :res[i]["n_hits"]]]
+        assert got == exp, (codes_to_str(w), lim, score)
+        assert (int(res[i]["d_best"]), int(res[i]["c0"]), int(res[i]["c1"])) == (d_best, c0, c1)
+        if exp:
+            assert int(res[i]["pad"]) == s1
+        assert bool(res[i]["flags"] & oracle.FLAG_MANY_BEST) == many
+        many_seen += many
+    if max_best:
+        assert many_seen > 0
+
+
 def test_positions_match_brute_force():
     t = _rand_text(400, 61)
     X = codes_to_str(t)
