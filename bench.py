@@ -526,7 +526,8 @@ def human_phase(args, aln, torch, dev, stream, flush):
         d = al.upload(w.reads.codes, w.reads.offsets, w.reads.lens, w.reads.z if per_read_z else None)
         res, hits = al.outputs(n, hit_cap)
         zkw = {"z": 6} if per_read_z else {}
-        pp = aln.Params.from_limits(w.params, hit_cap=hit_cap, mode=aln.MODE_PERSISTENT, **zkw)
+        pp = aln.Params.from_limits(w.params, hit_cap=hit_cap, mode=aln.MODE_PERSISTENT, l2_window=args.l2_window,
+                                    **zkw)
         pl = aln.Params.from_limits(w.params, hit_cap=hit_cap, mode=aln.MODE_PLAIN, **zkw)
         b = {"reads_per_step": n, "steps": args.human_steps, "warmup": args.human_warmup}
         graph = None
@@ -728,7 +729,8 @@ def run_gpu(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     modes = {"persistent": aln.MODE_PERSISTENT, "plain": aln.MODE_PLAIN}
     params = {k: aln.Params.from_limits(lim, hit_cap=hit_cap, mode=m, blocks_per_sm=args.blocks_per_sm,
-                                        work_limit=args.work_limit, **({"z": 6} if per_read_z else {}))
+                                        work_limit=args.work_limit, l2_window=args.l2_window if k == "persistent" else 0,
+                                        **({"z": 6} if per_read_z else {}))
               for k, m in modes.items()}
 
     tuned_ms = None
@@ -856,7 +858,9 @@ def run_gpu(args):
         "flags": flag_counts,
         "schedule": {"blocks_per_sm": params["persistent"].blocks_per_sm or "max",
                      "smem_stack": params["persistent"].smem_stack or 8,
-                     "help_after": params["persistent"].help_after or 4096,
+                     "help_after": params["persistent"].help_after or "once the read queue is empty",
+                     "heavy_after": params["persistent"].heavy_after or 2 ** 18,
+                     "l2_window": args.l2_window,
                      "autotune_ms": tuned_ms, "graph_replay": bool(graph is not None),
                      "reads_per_rank": [partition_range(n, r, ws)[1] - partition_range(n, r, ws)[0]
                                         for r in range(ws)]},
@@ -1018,6 +1022,8 @@ def main():
     ap.add_argument("--human-warmup", type=int, default=3)
     ap.add_argument("--human-serve-seconds", type=float, default=60.0)
     ap.add_argument("--human-serve-lambda", type=float, default=50.0)
+    ap.add_argument("--l2-window", type=int, default=0,
+                    help="1: hold the prefix-trie tables in L2's persisting set during the search (l2_window)")
     ap.add_argument("--index-build", default="gpu", choices=["gpu", "host"],
                     help="build the index with fm_index_build_gpu (default) or on the host cores")
     args = ap.parse_args()

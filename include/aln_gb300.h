@@ -70,6 +70,8 @@ extern "C" {
 #define ALN_FLAG_WORK_LIMIT 0x20     /* per-read expansion limit reached: incomplete */
 #define ALN_FLAG_LOOP_LIMIT 0x40     /* the persistent launch reached its loop bound before
                                         this read was finished: no hits, incomplete */
+#define ALN_FLAG_MANY_BEST 0x80      /* score-ordered mode: more than max_best places have the
+                                        best score; only the best score's hits are listed */
 #define ALN_FLAG_INCOMPLETE (ALN_FLAG_STACK_OVERFLOW | ALN_FLAG_CAND_OVERFLOW | ALN_FLAG_WORK_LIMIT | \
                              ALN_FLAG_LOOP_LIMIT)
 
@@ -82,6 +84,14 @@ extern "C" {
 #define ALN_MODE_PERSISTENT 1 /* one persistent launch; threads pull reads from a device queue */
 #define ALN_STRATA_BEST1 0    /* keep hits with diffs <= min(z, d_best + 1) */
 #define ALN_STRATA_FULL 1     /* keep every hit with diffs <= z */
+#define ALN_STRATA_SCORE 2    /* score-ordered (persistent form only): every hit within z with
+                                 its least witness by (score, diffs, gap opens, gap extensions,
+                                 mismatches, length), score = score_mm * n_mm + score_gapo *
+                                 n_gapo + score_gape * n_gape; S1 = the least score, S2 = the
+                                 least score above it; hits scoring S1 or S2 listed in the
+                                 order (score, strand, k, l) (S1 only, flag ALN_FLAG_MANY_BEST,
+                                 when c0 > max_best > 0); c0 / c1 = summed widths at S1 / S2;
+                                 d_best = fewest diffs among the S1 hits; best_score = S1 */
 
 typedef struct fm_index fm_index;   /* host-resident index (opaque) */
 typedef struct fm_dindex fm_dindex; /* device-resident index image (opaque) */
@@ -201,7 +211,10 @@ typedef struct {
                                heavy phase, which searches it with every lane of the GPU (up to
                                2048 reads per call; later ones stay with their warp); 0 = 2^18,
                                0xFFFFFFFF = never; result-neutral */
-    uint32_t reserved;
+    uint8_t score_mm;       /* score-ordered mode: mismatch penalty; 0 = 3 (with the two below: */
+    uint8_t score_gapo;     /*   gap-open penalty; 0 = 11       BWA's defaults) */
+    uint8_t score_gape;     /*   gap-extension penalty; 0 = 4 */
+    uint8_t max_best;       /* score-ordered mode: cap on places with the best score; 0 = none */
 } aln_params;
 
 #define ALN_SMEM_STACK_CHOICES {4, 8, 12}
@@ -225,7 +238,8 @@ typedef struct {
     uint8_t n_hits;         /* hits written (<= hit_cap) */
     uint8_t flags;          /* ALN_FLAG_* */
     uint8_t d_best;         /* fewest differences of any hit; 255 = no hit */
-    uint8_t reserved;
+    uint8_t best_score;     /* score-ordered mode: the best score S1 (at most 254; 255 = no
+                               hit); 0 in the other modes */
 } aln_read_result;
 
 typedef struct {

@@ -632,6 +632,7 @@ static uint64_t align_one(const orc_index *ix, const uint8_t *w, int m, int z, c
 {
     memset(res, 0, sizeof *res);
     res->d_best = 255;
+    if (p->strata == STRATA_SCORE) res->pad = 255; /* the best score, 255 while there is no hit */
     if (m > READ_MAX) { res->flags |= F_READ_TOO_LONG; return 0; }
     if (z > Z_MAX) { res->flags |= F_BAD_LIMIT; return 0; }
     uint64_t look = 0;

@@ -22,10 +22,10 @@ import numpy as np
 from . import _lib
 from ._lib import (  # noqa: F401
     ALN_ELIMIT, ALN_OK, AlnError, CAND_CAP, FLAG_BAD_LIMIT, FLAG_CAND_OVERFLOW, FLAG_HIT_OVERFLOW,
-    FLAG_INCOMPLETE, FLAG_LOOP_LIMIT, FLAG_READ_TOO_LONG, FLAG_STACK_OVERFLOW, FLAG_WORK_LIMIT,
+    FLAG_INCOMPLETE, FLAG_LOOP_LIMIT, FLAG_MANY_BEST, FLAG_READ_TOO_LONG, FLAG_STACK_OVERFLOW, FLAG_WORK_LIMIT,
     HIT_DTYPE, MAX_HIT_CAP, MAX_READ_LEN, MAX_Z, MODE_PERSISTENT, MODE_PLAIN, POS_BAD_HIT,
     POS_TOO_WIDE, POS_WALK_LIMIT, RES_DTYPE, SMEM_STACK_CHOICES, STATUS_LOOP_LIMIT, STRATA_BEST1,
-    STRATA_FULL, check, lib, library_path, PAIR_DTYPE, PAIR_MAPPED1, PAIR_MAPPED2, PAIR_PLACED1, PAIR_PLACED2,
+    STRATA_FULL, STRATA_SCORE, check, lib, library_path, PAIR_DTYPE, PAIR_MAPPED1, PAIR_MAPPED2, PAIR_PLACED1, PAIR_PLACED2,
     PAIR_UNIQUE, PAIR_PROPER, PAIR_DISCORDANT, PAIR_STATS_FIELDS,
 )
 
@@ -172,12 +172,17 @@ class Params:
     help_after: int = 0
     l2_window: int = 0
     heavy_after: int = 0
+    score_mm: int = 0
+    score_gapo: int = 0
+    score_gape: int = 0
+    max_best: int = 0
 
     def c(self) -> _lib.aln_params:
         return _lib.aln_params(self.z, self.max_gapo, self.max_gape, self.seed_len, self.seed_z,
                                self.indel_end_skip, self.hit_cap, self.mode, self.strata,
                                self.blocks_per_sm, self.smem_stack, self.l2_window, self.work_limit,
-                               self.loop_limit, self.help_after, self.heavy_after, 0)
+                               self.loop_limit, self.help_after, self.heavy_after, self.score_mm,
+                               self.score_gapo, self.score_gape, self.max_best)
 
     @classmethod
     def from_limits(cls, lim: dict, **kw) -> "Params":

@@ -26,12 +26,13 @@ FLAG_READ_TOO_LONG = 0x08
 FLAG_BAD_LIMIT = 0x10
 FLAG_WORK_LIMIT = 0x20
 FLAG_LOOP_LIMIT = 0x40
+FLAG_MANY_BEST = 0x80
 FLAG_INCOMPLETE = FLAG_STACK_OVERFLOW | FLAG_CAND_OVERFLOW | FLAG_WORK_LIMIT | FLAG_LOOP_LIMIT
 STATUS_LOOP_LIMIT = 0x1
 ALN_ELIMIT = -4
 SMEM_STACK_CHOICES = (4, 8, 12)
 MODE_PLAIN, MODE_PERSISTENT = 0, 1
-STRATA_BEST1, STRATA_FULL = 0, 1
+STRATA_BEST1, STRATA_FULL, STRATA_SCORE = 0, 1, 2
 POS_TOO_WIDE = 0xFFFFFFFF
 POS_WALK_LIMIT = 0xFFFFFFFE
 POS_BAD_HIT = 0xFFFFFFFD
@@ -47,7 +48,7 @@ HIT_DTYPE = np.dtype([("k", "<u4"), ("l", "<u4"), ("aligned_len", "<u2"), ("stra
                       ("n_diff", "u1"), ("n_mm", "u1"), ("n_gapo", "u1"), ("n_gape", "u1"),
                       ("reserved", "u1")])
 RES_DTYPE = np.dtype([("c0", "<u4"), ("c1", "<u4"), ("n_hits", "u1"), ("flags", "u1"),
-                      ("d_best", "u1"), ("reserved", "u1")])
+                      ("d_best", "u1"), ("best_score", "u1")])
 
 
 class fm_build_opts(ctypes.Structure):
@@ -76,7 +77,8 @@ class aln_params(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_uint8), ("smem_stack", ctypes.c_uint8),
                 ("l2_window", ctypes.c_uint8), ("work_limit", ctypes.c_uint32),
                 ("loop_limit", ctypes.c_uint32), ("help_after", ctypes.c_uint32),
-                ("heavy_after", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("heavy_after", ctypes.c_uint32), ("score_mm", ctypes.c_uint8), ("score_gapo", ctypes.c_uint8),
+                ("score_gape", ctypes.c_uint8), ("max_best", ctypes.c_uint8)]
 
 
 class aln_result(ctypes.Structure):

@@ -44,8 +44,10 @@ struct fm_dindex {
 static int search_params(const char *who, const aln_params &P, uint32_t n_reads, SearchParams &sp) {
     if (P.z > ALN_MAX_Z) return fail(ALN_EINVAL, std::string(who) + ": z > ALN_MAX_Z");
     if (P.hit_cap < 1) return fail(ALN_EINVAL, std::string(who) + ": hit_cap must be >= 1");
-    if (P.mode > ALN_MODE_PERSISTENT || P.strata > ALN_STRATA_FULL)
+    if (P.mode > ALN_MODE_PERSISTENT || P.strata > ALN_STRATA_SCORE)
         return fail(ALN_EINVAL, std::string(who) + ": bad mode or strata");
+    if (P.strata == ALN_STRATA_SCORE && P.mode != ALN_MODE_PERSISTENT)
+        return fail(ALN_EINVAL, std::string(who) + ": the score-ordered mode needs the persistent form");
     if (!smem_stack_supported(P.smem_stack))
         return fail(ALN_EINVAL, std::string(who) + ": smem_stack must be 0 or one of ALN_SMEM_STACK_CHOICES");
     sp.z = P.z;
@@ -61,6 +63,10 @@ static int search_params(const char *who, const aln_params &P, uint32_t n_reads,
     sp.smem_stack = P.smem_stack;
     sp.help_after = P.help_after ? P.help_after : kDefaultHelpAfter;
     sp.heavy_after = P.heavy_after ? P.heavy_after : kDefaultHeavyAfter;
+    sp.sc_mm = P.score_mm ? P.score_mm : 3;
+    sp.sc_go = P.score_gapo ? P.score_gapo : 11;
+    sp.sc_ge = P.score_gape ? P.score_gape : 4;
+    sp.max_best = P.max_best;
     sp.heavy.hdr = nullptr;
     if (P.l2_window > 1) return fail(ALN_EINVAL, std::string(who) + ": l2_window must be 0 or 1");
     sp.window_base = nullptr;

@@ -72,15 +72,17 @@ struct FlatLane {
     unsigned long long st_reads = 0, st_rounds = 0, st_pops = 0;
 #endif
 
-    __device__ __forceinline__ void add_cand(uint32_t lo, uint32_t hi, uint32_t key) {
+    // Record a candidate; equal (strand, lo, hi) keep the least (score, key)
+    // (the score is 0 outside the score-ordered mode).
+    __device__ __forceinline__ void add_cand(uint32_t lo, uint32_t hi, uint32_t key, uint32_t score) {
         for (uint32_t j = 0; j < nc; j++) {
             const uint4 c = cand[j];
             if (c.x == lo && c.y == hi && (c.z >> 31) == (key >> 31)) {
-                if (key < c.z) cand[j].z = key;
+                if (score < c.w || (score == c.w && key < c.z)) cand[j] = make_uint4(lo, hi, key, score);
                 return;
             }
         }
-        if (nc < kCandCap) cand[nc++] = make_uint4(lo, hi, key, 0);
+        if (nc < kCandCap) cand[nc++] = make_uint4(lo, hi, key, score);
         else flags |= ALN_FLAG_CAND_OVERFLOW;
     }
 
@@ -97,13 +99,88 @@ struct FlatLane {
         dcnt++;
     }
 
-    __device__ __forceinline__ void write_result(aln_read_result *res, aln_hit *hits, const SearchParams &p,
-                                                 bool any, uint32_t final_b) {
+    // Score-ordered mode: strata by penalty score (S1 and S2), order (score,
+    // strand, k, l), the S1 stratum alone above max_best best places.
+    __device__ void write_score_result(aln_read_result *res, aln_hit *hits, const SearchParams &p) {
         aln_read_result out;
         out.c0 = out.c1 = 0;
         out.n_hits = 0;
         out.d_best = 255;
-        out.reserved = 0;
+        out.best_score = 255;
+        aln_hit *H = hits + static_cast<uint64_t>(r) * p.hit_cap;
+        uint32_t s1 = 0xFFFFFFFFu, s2 = 0xFFFFFFFFu;
+        for (uint32_t j = 0; j < nc; j++) s1 = min(s1, cand[j].w);
+        for (uint32_t j = 0; j < nc; j++)
+            if (cand[j].w > s1) s2 = min(s2, cand[j].w);
+        unsigned long long c0 = 0, c1 = 0;
+        uint32_t dbest = 255;
+        for (uint32_t j = 0; j < nc; j++) {
+            const uint4 c = cand[j];
+            if (c.w == s1) {
+                c0 += c.y - c.x;
+                dbest = min(dbest, (c.z >> 28) & 7u);
+            } else if (c.w == s2) {
+                c1 += c.y - c.x;
+            }
+        }
+        const bool many = p.max_best && c0 > p.max_best;
+        uint32_t kept = 0;
+        for (uint32_t j = 0; j < nc; j++) {
+            const uint4 c = cand[j];
+            if (c.w == s1 || (!many && c.w == s2)) cand[kept++] = c;
+        }
+        if (many) flags |= ALN_FLAG_MANY_BEST;
+        const uint32_t nout = min(kept, p.hit_cap);
+        if (kept > p.hit_cap) flags |= ALN_FLAG_HIT_OVERFLOW;
+        for (uint32_t t = 0; t < nout; t++) {  // order (score, strand, k, l): selection
+            uint32_t best = t;
+            uint4 cb = cand[t];
+            for (uint32_t j = t + 1; j < kept; j++) {
+                const uint4 cj = cand[j];
+                if (cj.w < cb.w || (cj.w == cb.w && ((cj.z >> 31) < (cb.z >> 31) ||
+                    ((cj.z >> 31) == (cb.z >> 31) && (cj.x < cb.x || (cj.x == cb.x && cj.y < cb.y)))))) {
+                    best = j;
+                    cb = cj;
+                }
+            }
+            cand[best] = cand[t];
+            cand[t] = cb;
+            aln_hit h;
+            const uint32_t key = cb.z;
+            h.k = cb.x;
+            h.l = cb.y - 1;
+            h.aligned_len = static_cast<uint16_t>(key & 0xFFFFu);
+            h.strand = static_cast<uint8_t>(key >> 31);
+            h.n_diff = static_cast<uint8_t>((key >> 28) & 7u);
+            h.n_gapo = static_cast<uint8_t>((key >> 24) & 15u);
+            h.n_gape = static_cast<uint8_t>((key >> 20) & 15u);
+            h.n_mm = static_cast<uint8_t>((key >> 16) & 15u);
+            h.reserved = 0;
+            H[t] = h;
+        }
+        if (nc) {
+            out.c0 = c0 > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(c0);
+            out.c1 = c1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(c1);
+            out.d_best = static_cast<uint8_t>(dbest);
+            out.best_score = static_cast<uint8_t>(s1 > 254 ? 254 : s1);
+            out.n_hits = static_cast<uint8_t>(nout);
+        }
+        out.flags = static_cast<uint8_t>(flags);
+        res[r] = out;
+        phase = PH_IDLE;
+    }
+
+    __device__ __forceinline__ void write_result(aln_read_result *res, aln_hit *hits, const SearchParams &p,
+                                                 bool any, uint32_t final_b) {
+        if (p.strata == ALN_STRATA_SCORE) {
+            write_score_result(res, hits, p);
+            return;
+        }
+        aln_read_result out;
+        out.c0 = out.c1 = 0;
+        out.n_hits = 0;
+        out.d_best = 255;
+        out.best_score = 0;
         aln_hit *H = hits + static_cast<uint64_t>(r) * p.hit_cap;
         if (any) {
             uint32_t kept = 0, dbest = 255;
@@ -326,7 +403,7 @@ struct FlatLane {
                         write_result(res, hits, p, false, 0);
                         continue;
                     }
-                    start_pass(n, p.strata == ALN_STRATA_FULL ? z : min(z, lb + 1));
+                    start_pass(n, p.strata != ALN_STRATA_BEST1 ? z : min(z, lb + 1));
                     continue;
                 }
                 phase = PH_DSCAN;
@@ -360,7 +437,7 @@ struct FlatLane {
                         write_result(res, hits, p, false, 0);
                         continue;
                     }
-                    start_pass(n, p.strata == ALN_STRATA_FULL ? z : min(z, lb + 1));
+                    start_pass(n, p.strata != ALN_STRATA_BEST1 ? z : min(z, lb + 1));
                     continue;
                 }
                 // strand 0's D comes from X, strand 1's from X reversed
@@ -406,7 +483,7 @@ struct FlatLane {
                     phase = PH_IDLE;
                     continue;
                 }
-                if ((flags & ALN_FLAG_WORK_LIMIT) || p.strata == ALN_STRATA_FULL) {
+                if ((flags & ALN_FLAG_WORK_LIMIT) || p.strata != ALN_STRATA_BEST1) {
                     write_result(res, hits, p, nc > 0, z);
                     continue;
                 }
@@ -474,7 +551,9 @@ struct FlatLane {
         const uint32_t rem = B - diffs;
         if (i == m) {
             const uint32_t alen = m + (go + ge - ni) - ni;
-            if (alen >= 1) add_cand(e.x, e.y, (s << 31) | (diffs << 28) | (go << 24) | (ge << 20) | (mm << 16) | alen);
+            if (alen >= 1)
+                add_cand(e.x, e.y, (s << 31) | (diffs << 28) | (go << 24) | (ge << 20) | (mm << 16) | alen,
+                         p.strata == ALN_STRATA_SCORE ? p.sc_mm * mm + p.sc_go * go + p.sc_ge * ge : 0u);
             return false;
         }
         const uint32_t bp0 = s ? bpb0 : bpa0, bp1 = s ? bpb1 : bpa1;
@@ -557,6 +636,14 @@ struct FlatLane {
     __device__ __forceinline__ void exchange(uint32_t lane, const uint32_t *sbase, const uint32_t *snbase,
                                              uint32_t warp_col, uint32_t help_after) {
         const unsigned FULL = 0xFFFFFFFFu;
+        // one vote decides whether there is anything to hand over this trip: a
+        // returning helper, a lane without work, a read just handed to the heavy
+        // phase, or (with a finite help_after) a read heavy enough to share
+        const bool want = phase == PH_RETURN || phase == PH_FREE || (phase == PH_IDLE && heavy_seen) ||
+                          (flags & kFlagDemoted) || (phase == PH_DFS && work > help_after);
+#ifndef ALN_EXCHANGE_ALWAYS
+        if (!__any_sync(FULL, want)) return;
+#endif
         unsigned ret = __ballot_sync(FULL, phase == PH_RETURN);
         while (ret) {
             const uint32_t src = __ffs(ret) - 1;
@@ -566,10 +653,10 @@ struct FlatLane {
             const uint32_t has = __shfl_sync(FULL, (mine && ret_i < nc) ? 1u : 0u, src);
             const uint4 c = (mine && ret_i < nc) ? cand[ret_i] : make_uint4(0, 0, 0, 0);
             const uint32_t cx = __shfl_sync(FULL, c.x, src), cy = __shfl_sync(FULL, c.y, src),
-                           cz = __shfl_sync(FULL, c.z, src);
+                           cz = __shfl_sync(FULL, c.z, src), cw = __shfl_sync(FULL, c.w, src);
             const uint32_t hf = __shfl_sync(FULL, flags, src);
             if (lane == o) {
-                if (has) add_cand(cx, cy, cz);
+                if (has) add_cand(cx, cy, cz, cw);
                 else {
                     outstanding--;
                     flags |= hf & ALN_FLAG_INCOMPLETE;
@@ -624,7 +711,7 @@ struct FlatLane {
         out.c0 = out.c1 = 0;
         out.n_hits = 0;
         out.d_best = 255;
-        out.reserved = 0;
+        out.best_score = 0;
         if (role == ROLE_OWN && (phase == PH_DSCAN || phase == PH_DFS || phase == PH_WAIT)) {
             out.flags = static_cast<uint8_t>(flags | ALN_FLAG_LOOP_LIMIT);
             res[r] = out;
@@ -637,6 +724,23 @@ struct FlatLane {
         }
         phase = PH_FREE;
     }
+
+#ifdef ALN_PREFETCH
+    // The node the next trip will most likely expand is `next`: bring the Occ
+    // blocks of its two rows into L1 now, so that their loads overlap this trip's
+    // hand-over and the next trip's control work.
+    __device__ __forceinline__ void prefetch_next(const DIndex &X) {
+        if (!has_next || phase != PH_DFS) return;
+        const uint32_t info = next.z;
+        const uint32_t i = info & 0xFFu, go = (info >> 11) & 7u, ge = (info >> 14) & 7u, ni = (info >> 17) & 7u;
+        if (i == m || i + go + ge - 2 * ni < K) return;  // an emission, or a table node
+        const DText &T = s ? X.t[0] : X.t[1];
+        const uint4 *a = T.blocks + 4ull * (next.x / kRowsPerBlock);
+        const uint4 *b = T.blocks + 4ull * (next.y / kRowsPerBlock);
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(b));
+    }
+#endif
 
     __device__ __forceinline__ void apply(const DIndex &X, const uint32_t lo4[4], const uint32_t hi4[4]) {
         if (phase == PH_DSCAN) {
@@ -656,6 +760,9 @@ struct FlatLane {
             dj--;
         } else {
             push_children(lo4, hi4);
+#ifdef ALN_PREFETCH
+            prefetch_next(X);
+#endif
         }
     }
 };

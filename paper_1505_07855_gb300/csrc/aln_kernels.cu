@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
             st_ce += clock64() - k2;
         }
 #endif
-        if (__ballot_sync(0xFFFFFFFFu, L.phase != PH_FREE) == 0) break;
+        if (!__any_sync(0xFFFFFFFFu, L.phase != PH_FREE)) break;
     }
     if (at_limit) L.stop_at_limit(lane, n_reads, p, res, queue, order);
 #ifdef ALN_STATS
@@ -188,14 +188,15 @@ __device__ __forceinline__ unsigned long long mix_id(unsigned long long x) {
 
 // Insert candidate (lo, hi) of strand s with witness key; returns false if the
 // read's table for that strand is full.
-__device__ bool heavy_insert(const HeavyCtx &H, uint32_t hid, uint32_t s, uint32_t lo, uint32_t hi, uint32_t key) {
+__device__ bool heavy_insert(const HeavyCtx &H, uint32_t hid, uint32_t s, uint32_t lo, uint32_t hi, uint32_t key,
+                             uint32_t score) {
     HeavySlot *T = H.slots + (static_cast<uint64_t>(hid) * 2 + s) * kHeavySlots;
     const unsigned long long id = (static_cast<unsigned long long>(lo) << 32) | hi;
     uint32_t j = static_cast<uint32_t>(mix_id(id)) & (kHeavySlots - 1);
     for (uint32_t probe = 0; probe < kHeavySlots; probe++, j = (j + 1) & (kHeavySlots - 1)) {
         const unsigned long long old = atomicCAS(&T[j].id, 0ull, id);
         if (old == 0ull || old == id) {
-            atomicMin(&T[j].key, key);
+            atomicMin(&T[j].wkey, (static_cast<unsigned long long>(score) << 32) | key);
             if (old == 0ull) atomicAdd(&H.reads[hid].distinct[s], 1u);
             return true;
         }
@@ -212,7 +213,7 @@ __global__ void aln_heavy_start_kernel(SearchParams p, const uint2 *dbp, uint32_
     HeavySlot *T = H.slots + static_cast<uint64_t>(hid) * 2 * kHeavySlots;
     for (uint32_t j = threadIdx.x; j < 2 * kHeavySlots; j += blockDim.x) {
         T[j].id = 0ull;
-        T[j].key = 0xFFFFFFFFu;
+        T[j].wkey = ~0ull;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -220,7 +221,7 @@ __global__ void aln_heavy_start_kernel(SearchParams p, const uint2 *dbp, uint32_
         const uint2 a = dbp[2ull * R->r], b = dbp[2ull * R->r + 1];
         const uint32_t d0 = d_at(a.x, a.y, 0), d1 = d_at(b.x, b.y, 0);
         const uint32_t lb = min(d0, d1);
-        R->B = p.strata == ALN_STRATA_FULL ? R->z : min(R->z, lb + 1);
+        R->B = p.strata != ALN_STRATA_BEST1 ? R->z : min(R->z, lb + 1);
         R->state = 0;
         R->flags = 0;
         R->distinct[0] = R->distinct[1] = 0;
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
                 uint32_t f = L.flags & ALN_FLAG_INCOMPLETE;
                 for (uint32_t j = 0; j < L.nc; j++) {
                     const uint4 c = L.cand[j];
-                    if (!heavy_insert(H, hid, c.z >> 31, c.x, c.y, c.z)) f |= ALN_FLAG_CAND_OVERFLOW;
+                    if (!heavy_insert(H, hid, c.z >> 31, c.x, c.y, c.z, c.w)) f |= ALN_FLAG_CAND_OVERFLOW;
                 }
                 if (f) atomicOr(&H.reads[hid].flags, f);
                 atomicSub(&H.hdr->outstanding, 1u);
@@ -410,6 +411,94 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
     }
 }
 
+// Score-ordered result of a handed-over read from its tables (the rule of the
+// persistent search's score writer: strata S1 / S2, order (score, strand, k, l)).
+__device__ void heavy_write_score(const SearchParams &p, const HeavySlot *T, const HeavyRead *R, uint32_t n_used,
+                                  aln_read_result *res, aln_hit *hits) {
+    aln_read_result out;
+    out.c0 = out.c1 = 0;
+    out.n_hits = 0;
+    out.d_best = 255;
+    out.best_score = 255;
+    uint32_t flags = R->flags & 0xFFu;
+    uint32_t s1 = 0xFFFFFFFFu, s2 = 0xFFFFFFFFu;
+    for (uint32_t j = 0; j < 2 * kHeavySlots; j++)
+        if (T[j].id) s1 = min(s1, static_cast<uint32_t>(T[j].wkey >> 32));
+    for (uint32_t j = 0; j < 2 * kHeavySlots; j++)
+        if (T[j].id && static_cast<uint32_t>(T[j].wkey >> 32) > s1) s2 = min(s2, static_cast<uint32_t>(T[j].wkey >> 32));
+    if (n_used) {
+        unsigned long long c0 = 0, c1 = 0;
+        uint32_t dbest = 255;
+        for (uint32_t j = 0; j < 2 * kHeavySlots; j++) {
+            if (!T[j].id) continue;
+            const uint32_t sc = static_cast<uint32_t>(T[j].wkey >> 32);
+            const unsigned long long w = (T[j].id & 0xFFFFFFFFull) - (T[j].id >> 32);
+            if (sc == s1) {
+                c0 += w;
+                dbest = min(dbest, (static_cast<uint32_t>(T[j].wkey) >> 28) & 7u);
+            } else if (sc == s2) {
+                c1 += w;
+            }
+        }
+        const bool many = p.max_best && c0 > p.max_best;
+        uint32_t kept = 0;
+        for (uint32_t j = 0; j < 2 * kHeavySlots; j++) {
+            if (!T[j].id) continue;
+            const uint32_t sc = static_cast<uint32_t>(T[j].wkey >> 32);
+            if (sc == s1 || (!many && sc == s2)) kept++;
+        }
+        if (many) flags |= ALN_FLAG_MANY_BEST;
+        const uint32_t nout = min(kept, p.hit_cap);
+        if (kept > p.hit_cap) flags |= ALN_FLAG_HIT_OVERFLOW;
+        aln_hit *Hh = hits + static_cast<uint64_t>(R->r) * p.hit_cap;
+        // order (score, strand, k, l): each round takes the least entry above the previous one
+        unsigned long long prev_s = 0, prev_o = 0;
+        bool have_prev = false;
+        for (uint32_t t = 0; t < nout; t++) {
+            bool found = false;
+            unsigned long long bs = 0, bo = 0;
+            uint32_t bkey = 0;
+            for (uint32_t j = 0; j < 2 * kHeavySlots; j++) {
+                if (!T[j].id) continue;
+                const uint32_t sc = static_cast<uint32_t>(T[j].wkey >> 32);
+                if (!(sc == s1 || (!many && sc == s2))) continue;
+                const uint32_t key = static_cast<uint32_t>(T[j].wkey);
+                // (strand, k, l) as one number: strand above the 64-bit interval order
+                const unsigned long long o = T[j].id;
+                const unsigned long long ss = (static_cast<unsigned long long>(sc) << 1) | (key >> 31);
+                if (have_prev && (ss < prev_s || (ss == prev_s && o <= prev_o))) continue;
+                if (!found || ss < bs || (ss == bs && o < bo)) {
+                    found = true;
+                    bs = ss;
+                    bo = o;
+                    bkey = key;
+                }
+            }
+            aln_hit h;
+            h.k = static_cast<uint32_t>(bo >> 32);
+            h.l = static_cast<uint32_t>(bo) - 1;
+            h.aligned_len = static_cast<uint16_t>(bkey & 0xFFFFu);
+            h.strand = static_cast<uint8_t>(bkey >> 31);
+            h.n_diff = static_cast<uint8_t>((bkey >> 28) & 7u);
+            h.n_gapo = static_cast<uint8_t>((bkey >> 24) & 15u);
+            h.n_gape = static_cast<uint8_t>((bkey >> 20) & 15u);
+            h.n_mm = static_cast<uint8_t>((bkey >> 16) & 15u);
+            h.reserved = 0;
+            Hh[t] = h;
+            prev_s = bs;
+            prev_o = bo;
+            have_prev = true;
+        }
+        out.c0 = c0 > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(c0);
+        out.c1 = c1 > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(c1);
+        out.d_best = static_cast<uint8_t>(dbest);
+        out.best_score = static_cast<uint8_t>(s1 > 254 ? 254 : s1);
+        out.n_hits = static_cast<uint8_t>(nout);
+    }
+    out.flags = static_cast<uint8_t>(flags);
+    res[R->r] = out;
+}
+
 // One block per handed-over read after a pass: the iterative deepening rule on
 // its table; the result, or the next pass's budget, cleared tables and roots.
 __global__ void aln_heavy_decide_kernel(SearchParams p, const uint2 *dbp, uint32_t n_text, aln_read_result *res,
@@ -430,7 +519,7 @@ __global__ void aln_heavy_decide_kernel(SearchParams p, const uint2 *dbp, uint32
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < 2 * kHeavySlots; j += blockDim.x)
         if (T[j].id) {
-            atomicMin(&s_dmin, (T[j].key >> 28) & 7u);
+            atomicMin(&s_dmin, (static_cast<uint32_t>(T[j].wkey) >> 28) & 7u);
             atomicAdd(&s_n, 1u);
         }
     __syncthreads();
@@ -438,7 +527,7 @@ __global__ void aln_heavy_decide_kernel(SearchParams p, const uint2 *dbp, uint32
         const uint32_t z = R->z, B = R->B;
         uint32_t next = 0, fin = 0;
         if (s_n > static_cast<uint32_t>(kCandCap)) R->flags |= ALN_FLAG_CAND_OVERFLOW;
-        if ((R->flags & ALN_FLAG_INCOMPLETE) || p.strata == ALN_STRATA_FULL) {
+        if ((R->flags & ALN_FLAG_INCOMPLETE) || p.strata != ALN_STRATA_BEST1) {
             fin = z;
         } else if (s_n == 0) {
             if (B < z) next = min(z, B + 2);
@@ -460,7 +549,7 @@ __global__ void aln_heavy_decide_kernel(SearchParams p, const uint2 *dbp, uint32
     if (s_next) {  // next pass: clear the tables, then the roots
         for (uint32_t j = threadIdx.x; j < 2 * kHeavySlots; j += blockDim.x) {
             T[j].id = 0ull;
-            T[j].key = 0xFFFFFFFFu;
+            T[j].wkey = ~0ull;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -474,23 +563,28 @@ __global__ void aln_heavy_decide_kernel(SearchParams p, const uint2 *dbp, uint32
         return;
     }
     if (threadIdx.x != 0) return;
+    if (p.strata == ALN_STRATA_SCORE) {
+        heavy_write_score(p, T, R, s_n, res, hits);
+        R->state = 1;
+        return;
+    }
     // the result: hits with diffs <= the final budget, ordered (diffs, strand, k, l)
     const uint32_t fin = s_final;
     aln_read_result out;
     out.c0 = out.c1 = 0;
     out.n_hits = 0;
     out.d_best = 255;
-    out.reserved = 0;
+    out.best_score = 0;
     uint32_t dbest = 255;
     for (uint32_t j = 0; j < 2 * kHeavySlots; j++)
-        if (T[j].id && ((T[j].key >> 28) & 7u) <= fin) dbest = min(dbest, (T[j].key >> 28) & 7u);
+        if (T[j].id && ((static_cast<uint32_t>(T[j].wkey) >> 28) & 7u) <= fin) dbest = min(dbest, (static_cast<uint32_t>(T[j].wkey) >> 28) & 7u);
     uint32_t flags = R->flags & 0xFFu;
     if (dbest != 255 && s_n) {
         unsigned long long c0 = 0, c1 = 0;
         uint32_t kept = 0;
         for (uint32_t j = 0; j < 2 * kHeavySlots; j++) {
             if (!T[j].id) continue;
-            const uint32_t d = (T[j].key >> 28) & 7u;
+            const uint32_t d = (static_cast<uint32_t>(T[j].wkey) >> 28) & 7u;
             if (d > fin) continue;
             kept++;
             const unsigned long long w = (T[j].id & 0xFFFFFFFFull) - (T[j].id >> 32);
@@ -512,7 +606,7 @@ __global__ void aln_heavy_decide_kernel(SearchParams p, const uint2 *dbp, uint32
             uint32_t bk = 0, bl = 0, bkey = 0;
             for (uint32_t j = 0; j < 2 * kHeavySlots; j++) {
                 if (!T[j].id) continue;
-                const uint32_t key = T[j].key;
+                const uint32_t key = static_cast<uint32_t>(T[j].wkey);
                 const uint32_t d = (key >> 28) & 7u;
                 if (d > fin) continue;
                 const uint32_t k = static_cast<uint32_t>(T[j].id >> 32), l = static_cast<uint32_t>(T[j].id);

@@ -71,9 +71,9 @@ struct HeavyTask {  // 32 bytes
     uint4 node;
     uint32_t hid, s, pad0, pad1;
 };
-struct HeavySlot {  // 16 bytes: a candidate (lo, hi) of one strand with its least witness key
-    unsigned long long id;  // lo << 32 | hi; 0 = empty
-    uint32_t key, pad;
+struct HeavySlot {  // 16 bytes: a candidate (lo, hi) of one strand with its least witness
+    unsigned long long id;    // lo << 32 | hi; 0 = empty
+    unsigned long long wkey;  // score << 32 | witness key (score 0 outside the score-ordered mode)
 };
 struct HeavyCtx {
     HeavyHdr *hdr;
@@ -88,6 +88,7 @@ struct SearchParams {
     uint32_t smem_stack;            // persistent form: stack entries per lane in shared memory
     uint32_t help_after;            // persistent form: expansions after which a read takes idle lanes
     uint32_t heavy_after;           // persistent form: owner expansions after which a read goes to the heavy phase
+    uint32_t sc_mm, sc_go, sc_ge, max_best;  // score-ordered mode: penalties and the cap on best places
     HeavyCtx heavy;                 // heavy phase state (hdr == nullptr: no heavy phase)
     unsigned long long loop_limit;  // persistent form: loop trips per warp
     uint32_t *status;               // ALN_STATUS_* bits, or nullptr
@@ -293,7 +294,7 @@ struct Search {
         out.c0 = out.c1 = 0;
         out.n_hits = 0;
         out.d_best = 255;
-        out.reserved = 0;
+        out.best_score = 0;
         if (m > ALN_MAX_READ_LEN) flags |= ALN_FLAG_READ_TOO_LONG;
         if (z > ALN_MAX_Z || z > p.z) flags |= ALN_FLAG_BAD_LIMIT;
         if (flags || m == 0) {

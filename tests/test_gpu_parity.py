@@ -184,6 +184,36 @@ def test_pairs_recipe_parity(cuda):
     assert _positions_parity(pair, rg, hg, "pairs positions") > 5000
 
 
+@pytest.mark.parametrize("li,score,max_best", [(1, (3, 11, 4), 0), (4, (3, 11, 4), 2), (6, (1, 2, 1), 0),
+                                               (2, (2, 3, 1), 1)])
+def test_score_mode_parity(cuda, li, score, max_best):
+    """Score-ordered mode (hits ranked by mismatch / gap-open / gap-extension
+    penalties, best and second-best score strata, cap on equally best places)
+    against the oracle, in the persistent search and in the heavy phase, on
+    texts with and without repeats."""
+    lim = LIMITS[li]
+    rng = Rng(4000 + li, "score")
+    text = reference_iid(20_000, rng.sub("t"))
+    text[5000:5400] = text[1000:1400]  # a repeat, so that best places tie
+    text[9000:9400] = text[1000:1400]
+    pair = Pair(text, kmers=[0, 7])
+    m = [20, 36, 50, 36, 60, 76, 40][li]
+    reads = simulate_reads(text, 1500, m, rng.sub("r"), sub_rate=(0.02, 0.04), indel_rate=0.005,
+                           indel_lens=(1, 2), n_frac=0.05, z=lim["z"])
+    ro, ho, _ = oracle_align(pair.ox, reads, lim, 40, oracle.SCORE, score=score, max_best=max_best)
+    for k, heavy in ((0, 0), (7, 0), (7, 1)):
+        p = aln.Params.from_limits(lim, hit_cap=40, strata=aln.STRATA_SCORE, mode=aln.MODE_PERSISTENT,
+                                   score_mm=score[0], score_gapo=score[1], score_gape=score[2],
+                                   max_best=max_best, heavy_after=heavy)
+        rg, hg = pair.als[k].align(reads.codes, reads.offsets, reads.lens, p)
+        compare(rg, hg, ro, ho, what=f"score limits {li} kmer {k} heavy_after {heavy}")
+    if max_best:
+        assert (rg["flags"] & aln.FLAG_MANY_BEST).any()
+    with pytest.raises(aln.AlnError):  # the plain form has no score-ordered mode
+        pair.al.align(reads.codes, reads.offsets, reads.lens,
+                      aln.Params.from_limits(lim, strata=aln.STRATA_SCORE, mode=aln.MODE_PLAIN))
+
+
 def test_pairing_parity(cuda):
     """The pairing stage on the GPU (compaction, SA walk, aln_pair_resolve) against
     the oracle's pairing of its own search results: every field of every pair and

@@ -290,8 +290,7 @@ def test_score_mode_against_brute_force(case):
                for h in hits[i, :res[i]["n_hits"]]]
         assert got == exp, (codes_to_str(w), lim, score)
         assert (int(res[i]["d_best"]), int(res[i]["c0"]), int(res[i]["c1"])) == (d_best, c0, c1)
-        if exp:
-            assert int(res[i]["pad"]) == s1
+        assert int(res[i]["pad"]) == s1  # 255 without a hit
         assert bool(res[i]["flags"] & oracle.FLAG_MANY_BEST) == many
         many_seen += many
     if max_best:
