@@ -44,7 +44,9 @@ struct FetchReq {
     uint32_t toff;    // F_TABLE: first of the four children entries
 };
 
-template <int STACK_CAP, int SMEM>
+// SCORE: the score-ordered mode (candidates keyed by (score, witness)); its
+// kernels are separate instantiations, so the other modes carry none of its code.
+template <int STACK_CAP, int SMEM, bool SCORE = false>
 struct FlatLane {
     uint4 *sstk;              // entries 0..SMEM-1: shared memory, entry j at sstk[j * kThreads]
     uint4 *stk;               // entries SMEM..STACK_CAP-1: local memory
@@ -78,7 +80,11 @@ struct FlatLane {
         for (uint32_t j = 0; j < nc; j++) {
             const uint4 c = cand[j];
             if (c.x == lo && c.y == hi && (c.z >> 31) == (key >> 31)) {
-                if (score < c.w || (score == c.w && key < c.z)) cand[j] = make_uint4(lo, hi, key, score);
+                if constexpr (SCORE) {
+                    if (score < c.w || (score == c.w && key < c.z)) cand[j] = make_uint4(lo, hi, key, score);
+                } else {
+                    if (key < c.z) cand[j].z = key;
+                }
                 return;
             }
         }
@@ -172,7 +178,7 @@ struct FlatLane {
 
     __device__ __forceinline__ void write_result(aln_read_result *res, aln_hit *hits, const SearchParams &p,
                                                  bool any, uint32_t final_b) {
-        if (p.strata == ALN_STRATA_SCORE) {
+        if constexpr (SCORE) {  // the score-ordered mode has its own writer (and kernels)
             write_score_result(res, hits, p);
             return;
         }
@@ -553,7 +559,7 @@ struct FlatLane {
             const uint32_t alen = m + (go + ge - ni) - ni;
             if (alen >= 1)
                 add_cand(e.x, e.y, (s << 31) | (diffs << 28) | (go << 24) | (ge << 20) | (mm << 16) | alen,
-                         p.strata == ALN_STRATA_SCORE ? p.sc_mm * mm + p.sc_go * go + p.sc_ge * ge : 0u);
+                         SCORE ? p.sc_mm * mm + p.sc_go * go + p.sc_ge * ge : 0u);
             return false;
         }
         const uint32_t bp0 = s ? bpb0 : bpa0, bp1 = s ? bpb1 : bpa1;
@@ -653,7 +659,7 @@ struct FlatLane {
             const uint32_t has = __shfl_sync(FULL, (mine && ret_i < nc) ? 1u : 0u, src);
             const uint4 c = (mine && ret_i < nc) ? cand[ret_i] : make_uint4(0, 0, 0, 0);
             const uint32_t cx = __shfl_sync(FULL, c.x, src), cy = __shfl_sync(FULL, c.y, src),
-                           cz = __shfl_sync(FULL, c.z, src), cw = __shfl_sync(FULL, c.w, src);
+                           cz = __shfl_sync(FULL, c.z, src), cw = SCORE ? __shfl_sync(FULL, c.w, src) : 0u;
             const uint32_t hf = __shfl_sync(FULL, flags, src);
             if (lane == o) {
                 if (has) add_cand(cx, cy, cz, cw);
@@ -725,22 +731,6 @@ struct FlatLane {
         phase = PH_FREE;
     }
 
-#ifdef ALN_PREFETCH
-    // The node the next trip will most likely expand is `next`: bring the Occ
-    // blocks of its two rows into L1 now, so that their loads overlap this trip's
-    // hand-over and the next trip's control work.
-    __device__ __forceinline__ void prefetch_next(const DIndex &X) {
-        if (!has_next || phase != PH_DFS) return;
-        const uint32_t info = next.z;
-        const uint32_t i = info & 0xFFu, go = (info >> 11) & 7u, ge = (info >> 14) & 7u, ni = (info >> 17) & 7u;
-        if (i == m || i + go + ge - 2 * ni < K) return;  // an emission, or a table node
-        const DText &T = s ? X.t[0] : X.t[1];
-        const uint4 *a = T.blocks + 4ull * (next.x / kRowsPerBlock);
-        const uint4 *b = T.blocks + 4ull * (next.y / kRowsPerBlock);
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(b));
-    }
-#endif
 
     __device__ __forceinline__ void apply(const DIndex &X, const uint32_t lo4[4], const uint32_t hi4[4]) {
         if (phase == PH_DSCAN) {
@@ -760,9 +750,6 @@ struct FlatLane {
             dj--;
         } else {
             push_children(lo4, hi4);
-#ifdef ALN_PREFETCH
-            prefetch_next(X);
-#endif
         }
     }
 };

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kThreads) aln_plain_kernel(DIndex X, ReadBatch
 #define ALN_PERSISTENT_MIN_BLOCKS 6  // 6 resident blocks per SM (80 registers, 8 shared stack entries) measured best
 #endif
 
-template <int STACK_CAP, int SMEM>
+template <int STACK_CAP, int SMEM, bool SCORE>
 __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persistent_kernel(DIndex X, ReadBatch rb, uint32_t n_reads,
                                                                   SearchParams p, aln_read_result *res,
                                                                   aln_hit *hits, uint32_t *queue,
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
     uint32_t *sb = s_bases + threadIdx.x, *sn = s_nmask + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31u, warp_col = threadIdx.x & ~31u;
     uint4 stk[STACK_CAP - SMEM], cand[kCandCap];
-    FlatLane<STACK_CAP, SMEM> L;
+    FlatLane<STACK_CAP, SMEM, SCORE> L;
     L.sstk = s_stack + threadIdx.x;
     L.stk = stk;
     L.cand = cand;
@@ -231,7 +231,7 @@ __global__ void aln_heavy_start_kernel(SearchParams p, const uint2 *dbp, uint32_
     }
 }
 
-template <int STACK_CAP>
+template <int STACK_CAP, bool SCORE>
 __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy_pass_kernel(DIndex X, ReadBatch rb,
                                                                                            SearchParams p,
                                                                                            const uint2 *dbp) {
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
     const uint32_t lane = threadIdx.x & 31u, warp_col = threadIdx.x & ~31u;
     const unsigned FULL = 0xFFFFFFFFu;
     uint4 stk[STACK_CAP - SMEM], cand[kCandCap];
-    FlatLane<STACK_CAP, SMEM> L;
+    FlatLane<STACK_CAP, SMEM, SCORE> L;
     L.sstk = s_stack + threadIdx.x;
     L.stk = stk;
     L.cand = cand;
@@ -729,7 +729,7 @@ __global__ void aln_order_scatter_kernel(const uint2 *dbp, uint32_t n, const uin
 int stack_cap_for(uint32_t z) { return z <= 2 ? 19 : (z <= 4 ? 37 : 64); }
 HeavyCtx heavy_layout(void *scratch, uint32_t n);
 
-template <int CAP, int SMEM>
+template <int CAP, int SMEM, bool SCORE>
 static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
                               aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue,
                               void *scratch, cudaStream_t st) {
@@ -740,7 +740,7 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<CAP, SMEM>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<CAP, SMEM, SCORE>, kThreads, 0);
         if (p.blocks_per_sm && static_cast<int>(p.blocks_per_sm) < per_sm) per_sm = p.blocks_per_sm;
         if (per_sm < 1) per_sm = 1;
         uint32_t blocks = static_cast<uint32_t>(sms * per_sm);
@@ -782,20 +782,21 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
             attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            const cudaError_t e = cudaLaunchKernelEx(&cfg, aln_persistent_kernel<CAP, SMEM>, X, rb, n, p1, res, hits,
+            const cudaError_t e = cudaLaunchKernelEx(&cfg, aln_persistent_kernel<CAP, SMEM, SCORE>, X, rb, n, p1, res, hits,
                                                      queue, static_cast<const uint32_t *>(order),
                                                      static_cast<const uint2 *>(dbp));
             if (e != cudaSuccess) return e;
         } else {
-            aln_persistent_kernel<CAP, SMEM><<<blocks, kThreads, 0, st>>>(X, rb, n, p1, res, hits, queue, order, dbp);
+            aln_persistent_kernel<CAP, SMEM, SCORE><<<blocks, kThreads, 0, st>>>(X, rb, n, p1, res, hits, queue, order,
+                                                                                dbp);
         }
         if (pp.heavy.hdr) {  // the reads handed over, one deepening pass per launch over the whole GPU
             int hb = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hb, aln_heavy_pass_kernel<CAP>, kThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hb, aln_heavy_pass_kernel<CAP, SCORE>, kThreads, 0);
             const unsigned hgrid = static_cast<unsigned>(sms * (hb > 0 ? hb : 1));
             aln_heavy_start_kernel<<<kHeavyReads, 128, 0, st>>>(pp, dbp, X.t[0].n);
             for (uint32_t pass = 0; pass < kHeavyPasses; pass++) {
-                aln_heavy_pass_kernel<CAP><<<hgrid, kThreads, 0, st>>>(X, rb, pp, dbp);
+                aln_heavy_pass_kernel<CAP, SCORE><<<hgrid, kThreads, 0, st>>>(X, rb, pp, dbp);
                 aln_heavy_decide_kernel<<<kHeavyReads, 128, 0, st>>>(pp, dbp, X.t[0].n, res, hits,
                                                                     pass + 1 == kHeavyPasses ? 1 : 0);
             }
@@ -810,9 +811,9 @@ template <int SMEM>
 static int max_blocks_smem(uint32_t z) {
     int per_sm = 0;
     switch (stack_cap_for(z)) {
-        case 19: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<19, SMEM>, kThreads, 0); break;
-        case 37: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<37, SMEM>, kThreads, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<64, SMEM>, kThreads, 0); break;
+        case 19: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<19, SMEM, false>, kThreads, 0); break;
+        case 37: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<37, SMEM, false>, kThreads, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aln_persistent_kernel<64, SMEM, false>, kThreads, 0); break;
     }
     return per_sm;
 }
@@ -857,10 +858,12 @@ template <int CAP>
 static cudaError_t launch_smem(const DIndex &X, const ReadBatch &rb, uint32_t n, const SearchParams &p,
                                aln_read_result *res, aln_hit *hits, uint32_t mode, uint32_t *queue, void *scratch,
                                cudaStream_t st) {
+    if (p.strata == ALN_STRATA_SCORE)  // score-ordered kernels: the default stack depth only
+        return launch_cap<CAP, kSmemStackDefault, true>(X, rb, n, p, res, hits, mode, queue, scratch, st);
     switch (p.smem_stack) {
-        case 4: return launch_cap<CAP, 4>(X, rb, n, p, res, hits, mode, queue, scratch, st);
-        case 12: return launch_cap<CAP, 12>(X, rb, n, p, res, hits, mode, queue, scratch, st);
-        default: return launch_cap<CAP, kSmemStackDefault>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        case 4: return launch_cap<CAP, 4, false>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        case 12: return launch_cap<CAP, 12, false>(X, rb, n, p, res, hits, mode, queue, scratch, st);
+        default: return launch_cap<CAP, kSmemStackDefault, false>(X, rb, n, p, res, hits, mode, queue, scratch, st);
     }
 }
 
