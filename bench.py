@@ -403,6 +403,22 @@ def workload_config(name, w, n_per_step, ws, mode="persistent"):
             "parallelism": f"replicas{ws}" if ws > 1 else "single"}
 
 
+def search_launches(aln, params, scratch=True):
+    """Kernels one search launches (the same list whether launched directly or
+    replayed from a graph): the plain form one; the persistent form the search,
+    with scratch the D pre-pass and the two visit-order kernels before it, and
+    unless the heavy phase is off its start kernel and one pass and one decide
+    kernel per deepening pass after it."""
+    if params.mode == aln.MODE_PLAIN:
+        return 1
+    n = 1
+    if scratch:
+        n += 3
+        if params.heavy_after != 0xFFFFFFFF:
+            n += 1 + 2 * aln.HEAVY_PASSES
+    return n
+
+
 def time_search(al, d, params, res, hits, stream, flush, steps, warmup, torch, graph=None):
     """Mean device time (ms, CUDA events on the launching stream) of `steps`
     searches after `warmup` untimed ones, L2 flushed before each."""
@@ -538,7 +554,8 @@ def human_phase(args, aln, torch, dev, stream, flush):
             t = time.time()
             pp, tuned_ms = al.autotune(dsub, pp, res, hits, stream)
             b["autotune"] = {"blocks_per_sm": pp.blocks_per_sm, "smem_stack": pp.smem_stack,
-                             "sample_reads": ns, "sample_ms": tuned_ms, "s": time.time() - t}
+                             "help_after": pp.help_after, "sample_reads": ns, "sample_ms": tuned_ms,
+                             "s": time.time() - t}
             with torch.cuda.stream(stream):
                 graph = al.capture(d, pp, res, hits)
             b["graph_replay"] = True
@@ -556,7 +573,7 @@ def human_phase(args, aln, torch, dev, stream, flush):
                       "bit_identical_to_persistent_on_complete_reads": same}
         b["persistent_over_plain"] = ms_l / ms_p
         b["flags"] = _flag_counts(aln, rq)
-        b["gpu_launches_per_step"] = {"persistent": 4, "plain": 1}
+        b["gpu_launches_per_step"] = {"persistent": search_launches(aln, pp), "plain": search_launches(aln, pl)}
         b["_out"] = (w, rq, hq, ms_p)
         blocks[name] = b
         del d, res, hits, graph
@@ -859,15 +876,14 @@ def run_gpu(args):
         "schedule": {"blocks_per_sm": params["persistent"].blocks_per_sm or "max",
                      "smem_stack": params["persistent"].smem_stack or 8,
                      "help_after": params["persistent"].help_after or "once the read queue is empty",
-                     "heavy_after": params["persistent"].heavy_after or 2 ** 18,
+                     "heavy_after": params["persistent"].heavy_after or aln.HEAVY_AFTER_DEFAULT,
                      "l2_window": args.l2_window,
                      "autotune_ms": tuned_ms, "graph_replay": bool(graph is not None),
                      "reads_per_rank": [partition_range(n, r, ws)[1] - partition_range(n, r, ws)[0]
                                         for r in range(ws)]},
-        # timed region: per persistent step the D pre-pass, two visit-order
-        # kernels and the search (a graph replay runs the same four kernels),
-        # per plain step the one search kernel
-        "gpu_launches": args.steps * (4 + 1),
+        # timed regions: the persistent steps and the plain steps (search_launches)
+        "gpu_launches": args.steps * (search_launches(aln, params["persistent"])
+                                      + search_launches(aln, params["plain"])),
         "e2e": {"value": e2e_v, "unit": "reads/s", "h2d_bytes_per_step": int(h2d) * ws,
                 "d2h_bytes_per_step": int(d2h) * ws, "hits_compacted": "aln_compact_hits",
                 "compacted_hits_equal_search_hits": bool(e2e_same)},

@@ -206,11 +206,12 @@ typedef struct {
                                reads take its pending subtrees before they take new reads
                                (the lanes a heavy read gets); 0 or 0xFFFFFFFF = only once
                                the read queue is empty; result-neutral */
-    uint32_t heavy_after;   /* persistent form with a pre-pass scratch: once the lane owning a
-                               read has made this many expansions, the read is handed to the
-                               heavy phase, which searches it with every lane of the GPU (up to
-                               2048 reads per call; later ones stay with their warp); 0 = 2^18,
-                               0xFFFFFFFF = never; result-neutral */
+    uint32_t heavy_after;   /* persistent form with a pre-pass scratch: once the read queue is
+                               empty (the batch's tail), a read whose owning lane has made more
+                               than this many expansions is handed to the heavy phase, which
+                               searches it with every lane of the GPU (up to 2048 reads per
+                               call; later ones stay with their warp);
+                               0 = ALN_HEAVY_AFTER_DEFAULT, 0xFFFFFFFF = never; result-neutral */
     uint8_t score_mm;       /* score-ordered mode: mismatch penalty; 0 = 3 (with the two below: */
     uint8_t score_gapo;     /*   gap-open penalty; 0 = 11       BWA's defaults) */
     uint8_t score_gape;     /*   gap-extension penalty; 0 = 4 */
@@ -218,6 +219,9 @@ typedef struct {
 } aln_params;
 
 #define ALN_SMEM_STACK_CHOICES {4, 8, 12}
+#define ALN_HEAVY_AFTER_DEFAULT 262144/* heavy_after = 0 in aln_search */
+#define ALN_HEAVY_PASSES 5     /* deepening passes of the heavy phase (z <= 7): one pass and one
+                                  decide kernel each, after one start kernel */
 
 /* One hit, 16 bytes.  The witness (n_diff .. aligned_len) is the minimal one,
  * ordered by (n_diff, n_gapo, n_gape, n_mm, aligned_len), over every valid
@@ -432,7 +436,9 @@ typedef struct {
                                    this long for more requests; 0 = launch at once */
     uint32_t reserved;
     aln_params params;          /* limits (mode is forced to ALN_MODE_PERSISTENT); params.z also
-                                   bounds the per-read z of requests */
+                                   bounds the per-read z of requests; heavy_after 0 here means
+                                   no heavy phase (it would hold every SM, stalling the other
+                                   slots' batches), a nonzero value asks for it */
 } aln_server_config;
 
 typedef struct {

@@ -24,7 +24,7 @@ from ._lib import (  # noqa: F401
     ALN_ELIMIT, ALN_OK, AlnError, CAND_CAP, FLAG_BAD_LIMIT, FLAG_CAND_OVERFLOW, FLAG_HIT_OVERFLOW,
     FLAG_INCOMPLETE, FLAG_LOOP_LIMIT, FLAG_MANY_BEST, FLAG_READ_TOO_LONG, FLAG_STACK_OVERFLOW, FLAG_WORK_LIMIT,
     HIT_DTYPE, MAX_HIT_CAP, MAX_READ_LEN, MAX_Z, MODE_PERSISTENT, MODE_PLAIN, POS_BAD_HIT,
-    POS_TOO_WIDE, POS_WALK_LIMIT, RES_DTYPE, SMEM_STACK_CHOICES, STATUS_LOOP_LIMIT, STRATA_BEST1,
+    POS_TOO_WIDE, POS_WALK_LIMIT, RES_DTYPE, SMEM_STACK_CHOICES, HEAVY_AFTER_DEFAULT, HEAVY_PASSES, STATUS_LOOP_LIMIT, STRATA_BEST1,
     STRATA_FULL, STRATA_SCORE, check, lib, library_path, PAIR_DTYPE, PAIR_MAPPED1, PAIR_MAPPED2, PAIR_PLACED1, PAIR_PLACED2,
     PAIR_UNIQUE, PAIR_PROPER, PAIR_DISCORDANT, PAIR_STATS_FIELDS,
 )

@@ -31,6 +31,8 @@ FLAG_INCOMPLETE = FLAG_STACK_OVERFLOW | FLAG_CAND_OVERFLOW | FLAG_WORK_LIMIT | F
 STATUS_LOOP_LIMIT = 0x1
 ALN_ELIMIT = -4
 SMEM_STACK_CHOICES = (4, 8, 12)
+HEAVY_PASSES = 5
+HEAVY_AFTER_DEFAULT = 262144
 MODE_PLAIN, MODE_PERSISTENT = 0, 1
 STRATA_BEST1, STRATA_FULL, STRATA_SCORE = 0, 1, 2
 POS_TOO_WIDE = 0xFFFFFFFF

@@ -31,6 +31,7 @@ enum : uint32_t { F_NONE = 0, F_OCC = 1, F_TABLE = 2, F_ROOT = 3, F_ZERO = 4 };
 // lane-private flag bits above the ABI's (never written to a result)
 constexpr uint32_t kFlagHeavyTried = 0x100;  // the read asked for a heavy-phase slot
 constexpr uint32_t kFlagDemoted = 0x200;     // the read was handed to the heavy phase
+constexpr uint32_t kFlagDrained = 0x400;     // a lane of the warp found the read queue empty
 constexpr int kSmemStackDefault = 8;  // bottom stack entries per lane kept in shared memory
 
 // First entry of level j (strings of length j) in the prefix-trie table.
@@ -511,12 +512,15 @@ struct FlatLane {
                 start_pass(n, F);
                 continue;
             }
-            if (role == ROLE_OWN && work > p.heavy_after && p.heavy.hdr && !(flags & kFlagHeavyTried)) {
-                flags |= kFlagHeavyTried;  // hand the read to the heavy phase if it has room
+            if (role == ROLE_OWN && work > p.heavy_after && (flags & kFlagDrained) && p.heavy.hdr &&
+                !(flags & kFlagHeavyTried)) {
+                // the batch's tail: hand the read to the heavy phase if it has room
+                flags |= kFlagHeavyTried;
                 const uint32_t hid = atomicAdd(&p.heavy.hdr->n_heavy, 1u);
                 if (hid < kHeavyReads) {
                     HeavyRead *H = p.heavy.reads + hid;
                     H->r = r;
+                    H->B = B;  // the heavy phase resumes at this deepening pass
                     H->z = z;
                     H->m = m;
                     flags |= kFlagDemoted;
@@ -647,9 +651,7 @@ struct FlatLane {
         // phase, or (with a finite help_after) a read heavy enough to share
         const bool want = phase == PH_RETURN || phase == PH_FREE || (phase == PH_IDLE && heavy_seen) ||
                           (flags & kFlagDemoted) || (phase == PH_DFS && work > help_after);
-#ifndef ALN_EXCHANGE_ALWAYS
         if (!__any_sync(FULL, want)) return;
-#endif
         unsigned ret = __ballot_sync(FULL, phase == PH_RETURN);
         while (ret) {
             const uint32_t src = __ffs(ret) - 1;
@@ -689,6 +691,7 @@ struct FlatLane {
         unsigned heavym = __ballot_sync(FULL, can_give && (role == ROLE_HELP || work > help_after));
         unsigned freem = __ballot_sync(FULL, phase == PH_FREE);
         unsigned idlem = __ballot_sync(FULL, phase == PH_IDLE && heavy_seen);
+        if (freem) flags |= kFlagDrained;  // the queue is empty for good: heavy reads may be handed over
         heavy_seen = heavym != 0;
         while (freem && donm) {
             const uint32_t rcv = __ffs(freem) - 1, dnr = __ffs(donm) - 1;

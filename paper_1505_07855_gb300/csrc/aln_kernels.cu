@@ -204,8 +204,10 @@ __device__ bool heavy_insert(const HeavyCtx &H, uint32_t hid, uint32_t s, uint32
     return false;
 }
 
-// One block per handed-over read: its first pass budget, cleared tables, the
-// root of each strand the lower bound admits as a task.
+// One block per handed-over read: cleared tables and the root of each strand
+// the lower bound admits as a task, for the deepening pass the read was in when
+// it was handed over (R->B, written by its lane).  Each pass starts from the
+// root with no candidates, so the passes before it need not be searched again.
 __global__ void aln_heavy_start_kernel(SearchParams p, const uint2 *dbp, uint32_t n_text) {
     const HeavyCtx H = p.heavy;
     const uint32_t hid = blockIdx.x;
@@ -220,8 +222,6 @@ __global__ void aln_heavy_start_kernel(SearchParams p, const uint2 *dbp, uint32_
         HeavyRead *R = H.reads + hid;
         const uint2 a = dbp[2ull * R->r], b = dbp[2ull * R->r + 1];
         const uint32_t d0 = d_at(a.x, a.y, 0), d1 = d_at(b.x, b.y, 0);
-        const uint32_t lb = min(d0, d1);
-        R->B = p.strata != ALN_STRATA_BEST1 ? R->z : min(R->z, lb + 1);
         R->state = 0;
         R->flags = 0;
         R->distinct[0] = R->distinct[1] = 0;
@@ -265,7 +265,10 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
     uint32_t hid = 0;
     const uint32_t n_heavy = min(vload(&H.hdr->n_heavy), kHeavyReads);
     if (n_heavy == 0) return;
-    const uint32_t low_water = 2u * gridDim.x * kThreads;  // ring entries kept available
+#ifndef ALN_HEAVY_LOW_DIV
+#define ALN_HEAVY_LOW_DIV 1
+#endif
+    const uint32_t low_water = 2u * gridDim.x * kThreads / ALN_HEAVY_LOW_DIV;  // ring entries kept available
     uint32_t idle_trips = 0;  // consecutive trips with no lane of the warp at work (warp-uniform)
     for (unsigned long long it = 0;; it++) {
         if (it >= p.loop_limit || idle_trips >= (1u << 23)) {  // guard: unfinished tasks mark their reads, the warp stops
@@ -301,6 +304,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
                     if (!heavy_insert(H, hid, c.z >> 31, c.x, c.y, c.z, c.w)) f |= ALN_FLAG_CAND_OVERFLOW;
                 }
                 if (f) atomicOr(&H.reads[hid].flags, f);
+                atomicAdd(&H.hdr->expansions, static_cast<unsigned long long>(L.work));
                 atomicSub(&H.hdr->outstanding, 1u);
                 L.phase = PH_IDLE;
                 break;
@@ -326,7 +330,9 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
             L.base++;
             heavy_push(H, e, hid, L.s);
         }
+#ifndef ALN_HEAVY_NO_EXCHANGE
         L.exchange(lane, s_bases, s_nmask, warp_col, 0u);
+#endif
         // idle lanes take tasks from the ring, one claim per warp
         const unsigned idle = __ballot_sync(FULL, L.phase == PH_IDLE);
         if (idle) {

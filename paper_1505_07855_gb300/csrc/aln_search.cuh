@@ -35,7 +35,7 @@ constexpr int kMaskWords = 8;   // N-mask words
 constexpr int kCandCap = ALN_CAND_CAP;
 constexpr uint32_t kDefaultWorkLimit = 1u << 24;
 constexpr uint32_t kDefaultHelpAfter = 0xFFFFFFFFu;  // only once the read queue is empty
-constexpr uint32_t kDefaultHeavyAfter = 1u << 18;
+constexpr uint32_t kDefaultHeavyAfter = ALN_HEAVY_AFTER_DEFAULT;
 
 enum : uint32_t { OP_M = 0, OP_I = 1, OP_D = 2 };
 
@@ -52,14 +52,16 @@ struct ReadBatch {
 constexpr uint32_t kHeavyReads = 2048;     // reads the heavy phase takes per call
 constexpr uint32_t kHeavySlots = 1024;     // candidate hash slots per read and strand
 constexpr uint32_t kHeavyPool = 1u << 20;  // task ring capacity
-constexpr uint32_t kHeavyPasses = 5;       // deepening passes launched (enough for z <= 7)
+constexpr uint32_t kHeavyPasses = ALN_HEAVY_PASSES;  // deepening passes launched (enough for z <= 7)
 
 struct HeavyHdr {   // 256 bytes
     uint32_t n_heavy;      // reads handed over (may pass kHeavyReads: those stay in the first phase)
     uint32_t head, tail;   // task ring tickets: taken, published
     uint32_t outstanding;  // tasks of the current pass not yet finished
-    uint32_t pad[60];
+    unsigned long long expansions;  // node expansions made by the heavy phase's tasks (a statistic)
+    uint32_t pad[58];
 };
+static_assert(sizeof(HeavyHdr) == 256, "heavy header layout");
 struct HeavyRead {  // 64 bytes
     uint32_t r, B, z, m;   // read index, pass budget, difference limit, length
     uint32_t state;        // 0 searching, 1 result written

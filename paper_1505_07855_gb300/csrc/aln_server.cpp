@@ -173,6 +173,10 @@ static int launch_slot(aln_server *S, Slot &s) {
     aln_batch b{s.d_bases, s.d_nmask, s.d_off, s.d_len, s.d_z};
     aln_params p = S->cfg.params;
     p.mode = ALN_MODE_PERSISTENT;
+    // the heavy phase holds every SM until its passes end, which stalls the
+    // batches of the other slots; here those batches fill the GPU while a heavy
+    // read finishes on its warp, so the phase runs only when asked for
+    if (p.heavy_after == 0) p.heavy_after = 0xFFFFFFFFu;
     aln_result out{s.d_res, s.d_hits};
     int rc = aln_search(S->idx, &b, n, &p, &out, st);
     if (rc != ALN_OK) return rc;

@@ -204,3 +204,34 @@ def test_server_argument_errors():
     assert L.aln_server_submit(None, None, None, None, None, 0, ctypes.byref(rid)) == -1
     assert L.aln_server_poll(None, 1, 0, None, None, None) == -1
     L.aln_server_destroy(None)
+
+
+def _header_macros():
+    vals = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^#define\s+ALN_(\w+)\s+(.+?)\s*$", src, re.M):
+            vals[m.group(1)] = m.group(2)
+    return vals
+
+
+def test_binding_constants_equal_the_header_macros():
+    """Every constant of the binding named after a header macro (ALN_X -> X or
+    ALN_X) carries the macro's value, so the two cannot drift apart."""
+    macros = _header_macros()
+    checked = 0
+    for name, text in macros.items():
+        py_name = name if hasattr(aln._lib, name) else "ALN_" + name
+        if not hasattr(aln._lib, py_name):
+            continue
+        py = getattr(aln._lib, py_name)
+        text = text.rstrip("uU")
+        if text.startswith("{"):
+            assert tuple(int(v) for v in text.strip("{}").split(",")) == tuple(py), name
+        elif re.fullmatch(r"\(?-?(0x[0-9A-Fa-f]+|\d+)u?\)?", text):
+            assert int(text.strip("()").rstrip("uU"), 0) == py, name
+        else:
+            continue
+        checked += 1
+    assert checked >= 20
+    assert aln.HEAVY_PASSES == int(macros["HEAVY_PASSES"])

@@ -46,9 +46,12 @@ def _same(a, b, cap):
         assert np.array_equal(np.where(valid, ha[f], 0), np.where(valid, hb[f], 0)), f
 
 
-def test_server_matches_direct_and_alone_equals_mixed(setup):
+@pytest.mark.parametrize("heavy_after", [0, 1])
+def test_server_matches_direct_and_alone_equals_mixed(setup, heavy_after):
+    """heavy_after 0: the server runs no heavy phase; 1: every batch's tail reads
+    go to the heavy phase, while other slots' batches are in flight."""
     w, dix = setup
-    params = aln.Params.from_limits(w.params, hit_cap=8, mode=aln.MODE_PERSISTENT, z=6)
+    params = aln.Params.from_limits(w.params, hit_cap=8, mode=aln.MODE_PERSISTENT, z=6, heavy_after=heavy_after)
     reqs = _requests(w, 24, 3)
     al = aln.Aligner(dix)
     direct = [al.align(r.codes, r.offsets, r.lens, params, z=r.z) for r in reqs]
