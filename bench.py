@@ -554,7 +554,7 @@ def human_phase(args, aln, torch, dev, stream, flush):
             t = time.time()
             pp, tuned_ms = al.autotune(dsub, pp, res, hits, stream)
             b["autotune"] = {"blocks_per_sm": pp.blocks_per_sm, "smem_stack": pp.smem_stack,
-                             "help_after": pp.help_after, "sample_reads": ns, "sample_ms": tuned_ms,
+                             "sample_reads": ns, "sample_ms": tuned_ms,
                              "s": time.time() - t}
             with torch.cuda.stream(stream):
                 graph = al.capture(d, pp, res, hits)

@@ -205,7 +205,8 @@ typedef struct {
                                many node expansions, lanes of its warp that finish their own
                                reads take its pending subtrees before they take new reads
                                (the lanes a heavy read gets); 0 or 0xFFFFFFFF = only once
-                               the read queue is empty; result-neutral */
+                               the read queue is empty; result-neutral.  heavy_after counts
+                               the owner's own expansions, so early help delays hand-over */
     uint32_t heavy_after;   /* persistent form with a pre-pass scratch: once the read queue is
                                empty (the batch's tail), a read whose owning lane has made more
                                than this many expansions is handed to the heavy phase, which
@@ -219,7 +220,7 @@ typedef struct {
 } aln_params;
 
 #define ALN_SMEM_STACK_CHOICES {4, 8, 12}
-#define ALN_HEAVY_AFTER_DEFAULT 262144/* heavy_after = 0 in aln_search */
+#define ALN_HEAVY_AFTER_DEFAULT 65536 /* heavy_after = 0 in aln_search */
 #define ALN_HEAVY_PASSES 5     /* deepening passes of the heavy phase (z <= 7): one pass and one
                                   decide kernel each, after one start kernel */
 
@@ -305,14 +306,16 @@ int aln_search(const fm_dindex *idx, const aln_batch *batch, uint32_t n_reads,
 uint64_t aln_search_scratch_bytes(uint32_t n_reads);
 
 /* Autotuner for the persistent form (the scheduler's knobs: how many lanes are
- * resident, how deep each lane's shared-memory stack is, how soon a heavy read
- * gets more lanes).  Times aln_search of a sample batch (device memory, laid out
- * as for aln_search; scratch receives its results): every resident-blocks-per-SM
- * value from 1 to what fits for every shared-memory stack depth of
- * ALN_SMEM_STACK_CHOICES (one warm-up run per depth), then help_after in
- * {1024, 4096, 16384, 0xFFFFFFFF} at the best of those; writes the fastest
- * blocks_per_sm, smem_stack and help_after into params (its time in *best_ms,
- * may be NULL).  The remaining fields of params are used as given.  The choice
+ * resident and how deep each lane's shared-memory stack is).  Times aln_search
+ * of a sample batch (device memory, laid out as for aln_search; scratch
+ * receives its results): every resident-blocks-per-SM value from 1 to what
+ * fits for every shared-memory stack depth of ALN_SMEM_STACK_CHOICES (one
+ * warm-up run per depth); writes the fastest blocks_per_sm and smem_stack into
+ * params (its time in *best_ms, may be NULL).  The remaining fields of params
+ * are used as given: help_after and heavy_after are not tuned (a sample's
+ * tail says little about a batch's, and lanes that help a read early keep its
+ * owner's expansions below heavy_after, so that it never reaches the heavy
+ * phase).  The choice
  * is cached per (index, sample size, sample z array, limits): a repeated call
  * returns it without timing.  Blocks on stream.  ALN_EINVAL for an empty
  * sample. */

@@ -256,15 +256,14 @@ class Aligner:
 
     def autotune(self, d, params: Params, res, hits, stream=None) -> tuple:
         """aln_autotune on an uploaded sample: returns (params with the fastest
-        blocks_per_sm, smem_stack and help_after, its time in ms)."""
+        blocks_per_sm and smem_stack, its time in ms)."""
         b = _lib.aln_batch(_ptr(d["bases"]), _ptr(d["nmask"]), _ptr(d["offsets"]), _ptr(d["lens"]), _ptr(d["z"]))
         r = _lib.aln_result(_ptr(res), _ptr(hits), _ptr(self.status), None, 0)
         p = params.c()
         ms = ctypes.c_float()
         check(lib().aln_autotune(self.dix._h, ctypes.byref(b), d["n"], ctypes.byref(p), ctypes.byref(r),
                                  _stream_ptr(stream), ctypes.byref(ms)), "aln_autotune")
-        return dataclasses.replace(params, blocks_per_sm=p.blocks_per_sm, smem_stack=p.smem_stack,
-                                   help_after=p.help_after), ms.value
+        return dataclasses.replace(params, blocks_per_sm=p.blocks_per_sm, smem_stack=p.smem_stack), ms.value
 
     def capture(self, d, params: Params, res, hits):
         """Capture one search of the uploaded batch d into a CUDA graph; replay it

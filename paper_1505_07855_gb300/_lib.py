@@ -32,7 +32,7 @@ STATUS_LOOP_LIMIT = 0x1
 ALN_ELIMIT = -4
 SMEM_STACK_CHOICES = (4, 8, 12)
 HEAVY_PASSES = 5
-HEAVY_AFTER_DEFAULT = 262144
+HEAVY_AFTER_DEFAULT = 65536
 MODE_PLAIN, MODE_PERSISTENT = 0, 1
 STRATA_BEST1, STRATA_FULL, STRATA_SCORE = 0, 1, 2
 POS_TOO_WIDE = 0xFFFFFFFF

@@ -355,7 +355,7 @@ extern "C" int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint3
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = ALN_OK, best_b = 0, best_s = 0;
-    uint32_t best_h = params->help_after ? params->help_after : kDefaultHelpAfter;  // what the first sweep ran with
+    const uint32_t best_h = params->help_after;
     float best = 0;
     auto timed = [&](float *ms) {
         cudaEventRecord(e0, st);
@@ -366,7 +366,9 @@ extern "C" int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint3
         cudaEventElapsedTime(ms, e0, e1);
         return r;
     };
-    // resident blocks per SM x shared-memory stack depth, then the heavy-read help threshold
+    // resident blocks per SM x shared-memory stack depth (help_after and heavy_after
+    // stay as given: lanes that help a read early keep its owner's expansion
+    // count below heavy_after, and a heavy read then never reaches the heavy phase)
     static const int kSmem[] = ALN_SMEM_STACK_CHOICES;
     for (int smem : kSmem) {
         const int maxb = persistent_max_blocks(params->z, static_cast<uint32_t>(smem));
@@ -382,19 +384,6 @@ extern "C" int aln_autotune(const fm_dindex *idx, const aln_batch *sample, uint3
                 best_b = b;
                 best_s = smem;
             }
-        }
-    }
-    static const uint32_t kHelp[] = {1024u, 4096u, 16384u, 0xFFFFFFFFu};  // the first sweep ran with the given value
-    p.blocks_per_sm = static_cast<uint8_t>(best_b);
-    p.smem_stack = static_cast<uint8_t>(best_s);
-    for (uint32_t h : kHelp) {
-        if (rc != ALN_OK) break;
-        p.help_after = h;
-        float ms = 0;
-        rc = timed(&ms);
-        if (rc == ALN_OK && ms < best) {
-            best = ms;
-            best_h = h;
         }
     }
     cudaEventDestroy(e0);

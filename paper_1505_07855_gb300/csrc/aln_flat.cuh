@@ -619,6 +619,7 @@ struct FlatLane {
         const uint32_t o = __shfl_sync(FULL, role == ROLE_OWN ? lane : owner, dnr);
         const uint32_t hm = __shfl_sync(FULL, m, dnr), hB = __shfl_sync(FULL, B, dnr);
         const uint32_t hs = __shfl_sync(FULL, s, dnr), hz = __shfl_sync(FULL, z, dnr);
+        const uint32_t hr = __shfl_sync(FULL, r, dnr);  // the read (the heavy phase: its list entry)
         const uint32_t h0 = __shfl_sync(FULL, s ? bpb0 : bpa0, dnr);
         const uint32_t h1 = __shfl_sync(FULL, s ? bpb1 : bpa1, dnr);
         if (giver) base++;
@@ -626,6 +627,7 @@ struct FlatLane {
         if (lane == rcv) {
             role = ROLE_HELP;
             owner = o;
+            r = hr;
             m = hm;
             B = hB;
             s = hs;

@@ -163,6 +163,12 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_persi
 // deepening rule to the table and either writes the result or starts the next
 // pass.  The hit set, witnesses and counts are those of the other forms.
 
+__device__ __forceinline__ unsigned long long global_ns() {  // the GPU's nanosecond timer
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ uint32_t vload(const uint32_t *p) { return *reinterpret_cast<const volatile uint32_t *>(p); }
 
 // Task t is published once its slot is written: ready[t % cap] = t + 1.
@@ -193,11 +199,24 @@ __device__ bool heavy_insert(const HeavyCtx &H, uint32_t hid, uint32_t s, uint32
     HeavySlot *T = H.slots + (static_cast<uint64_t>(hid) * 2 + s) * kHeavySlots;
     const unsigned long long id = (static_cast<unsigned long long>(lo) << 32) | hi;
     uint32_t j = static_cast<uint32_t>(mix_id(id)) & (kHeavySlots - 1);
+    const unsigned long long wkey = (static_cast<unsigned long long>(score) << 32) | key;
+    // Many lanes insert the same few intervals of a repeat-rich read: a plain
+    // read first skips the atomics that would change nothing.  Safe with a stale
+    // value: a slot's id only goes from 0 to its final value, and its key only
+    // decreases, so a stale read can only cause an atomic, never skip one that
+    // was needed.
     for (uint32_t probe = 0; probe < kHeavySlots; probe++, j = (j + 1) & (kHeavySlots - 1)) {
-        const unsigned long long old = atomicCAS(&T[j].id, 0ull, id);
-        if (old == 0ull || old == id) {
-            atomicMin(&T[j].wkey, (static_cast<unsigned long long>(score) << 32) | key);
-            if (old == 0ull) atomicAdd(&H.reads[hid].distinct[s], 1u);
+        unsigned long long cur = __ldcg(&T[j].id);
+        if (cur == 0ull) {
+            cur = atomicCAS(&T[j].id, 0ull, id);
+            if (cur == 0ull) {
+                atomicMin(&T[j].wkey, wkey);
+                atomicAdd(&H.reads[hid].distinct[s], 1u);
+                return true;
+            }
+        }
+        if (cur == id) {
+            if (__ldcg(&T[j].wkey) > wkey) atomicMin(&T[j].wkey, wkey);
             return true;
         }
     }
@@ -265,13 +284,19 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
     uint32_t hid = 0;
     const uint32_t n_heavy = min(vload(&H.hdr->n_heavy), kHeavyReads);
     if (n_heavy == 0) return;
-#ifndef ALN_HEAVY_LOW_DIV
-#define ALN_HEAVY_LOW_DIV 1
-#endif
-    const uint32_t low_water = 2u * gridDim.x * kThreads / ALN_HEAVY_LOW_DIV;  // ring entries kept available
-    uint32_t idle_trips = 0;  // consecutive trips with no lane of the warp at work (warp-uniform)
+    // Ring entries kept available: one per warp of the grid, so that owners
+    // split their subtrees only while lanes wait for work (a mark of two per
+    // lane cut them into tasks of about 128 expansions and ran longer).  The
+    // ring then holds at most low_water + 32 per warp, within its capacity
+    // (the launch bounds the grid).
+    const uint32_t low_water = gridDim.x * (kThreads / 32u);
+    // consecutive trips with no lane of the warp at work, and since when (warp-uniform)
+    uint32_t idle_trips = 0;
+    unsigned long long idle_since = 0;
+    bool idle_expired = false;
+    uint32_t trips = 0, busy = 0;  // this lane's trips, and those it spent on a task
     for (unsigned long long it = 0;; it++) {
-        if (it >= p.loop_limit || idle_trips >= (1u << 23)) {  // guard: unfinished tasks mark their reads, the warp stops
+        if (it >= p.loop_limit || idle_expired) {  // guard: unfinished tasks mark their reads, the warp stops
             if (lane == 0 && p.status) atomicOr(p.status, ALN_STATUS_LOOP_LIMIT);
             if (L.role == ROLE_OWN && L.phase != PH_IDLE && L.phase != PH_FREE)
                 atomicOr(&H.reads[hid].flags, ALN_FLAG_LOOP_LIMIT);
@@ -279,6 +304,8 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
         }
         FetchReq fr;
         fr.kind = F_NONE;
+        trips++;
+        busy += (L.phase != PH_IDLE && L.phase != PH_FREE) ? 1u : 0u;
         // control: advance the lane's task until it needs four extensions
         for (int round = 0; round < 32; round++) {
             if (L.phase == PH_FREE || L.phase == PH_RETURN || L.phase == PH_IDLE) break;
@@ -323,16 +350,46 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
             fetch4(X, fr, lo4, hi4);
             L.apply(X, lo4, hi4);
         }
-        // the ring runs low: a task owner gives its bottom stack entry back to it
-        if (L.role == ROLE_OWN && L.phase == PH_DFS && (L.sp - L.base >= 2 || (L.sp - L.base >= 1 && L.has_next)) &&
-            vload(&H.hdr->tail) - vload(&H.hdr->head) < low_water) {
-            const uint4 e = L.stk_get(L.base);
-            L.base++;
-            heavy_push(H, e, hid, L.s);
+        // the ring runs low: task owners give their bottom stack entries back to
+        // it (its level read by one lane, the tickets taken once per warp)
+        const bool can_push = L.role == ROLE_OWN && L.phase == PH_DFS &&
+                              (L.sp - L.base >= 2 || (L.sp - L.base >= 1 && L.has_next));
+        const unsigned pushers = __ballot_sync(FULL, can_push);
+        if (pushers) {
+            const uint32_t src = __ffs(pushers) - 1;
+            uint32_t t0 = 0xFFFFFFFFu;
+            if (lane == src && vload(&H.hdr->tail) - vload(&H.hdr->head) < low_water) {
+                atomicAdd(&H.hdr->outstanding, static_cast<uint32_t>(__popc(pushers)));  // before publishing
+                t0 = atomicAdd(&H.hdr->tail, static_cast<uint32_t>(__popc(pushers)));
+            }
+            t0 = __shfl_sync(FULL, t0, src);
+            if (t0 != 0xFFFFFFFFu && can_push) {
+                const uint32_t t = t0 + __popc(pushers & ((1u << lane) - 1u));
+                const uint4 e = L.stk_get(L.base);
+                L.base++;
+                HeavyTask task;
+                task.node = e;
+                task.hid = hid;
+                task.s = L.s;
+                task.pad0 = task.pad1 = 0;
+                H.pool[t % kHeavyPool] = task;
+                __threadfence();
+                atomicExch(&H.ready[t % kHeavyPool], t + 1u);
+            }
         }
-#ifndef ALN_HEAVY_NO_EXCHANGE
+        // a helper merges its candidates into the read's table itself: the
+        // hand-back through the owner moves one per trip, and a subtree of a
+        // repeat-rich read can hold hundreds
+        if (L.phase == PH_RETURN && L.ret_i < L.nc) {
+            uint32_t f = 0;
+            for (uint32_t j = L.ret_i; j < L.nc; j++) {
+                const uint4 c = L.cand[j];
+                if (!heavy_insert(H, L.r, c.z >> 31, c.x, c.y, c.z, c.w)) f |= ALN_FLAG_CAND_OVERFLOW;
+            }
+            if (f) atomicOr(&H.reads[L.r].flags, f);
+            L.ret_i = L.nc;
+        }
         L.exchange(lane, s_bases, s_nmask, warp_col, 0u);
-#endif
         // idle lanes take tasks from the ring, one claim per warp
         const unsigned idle = __ballot_sync(FULL, L.phase == PH_IDLE);
         if (idle) {
@@ -375,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
                         task.s = __ldcg(&slot->s);
                         hid = task.hid;
                         const HeavyRead R = H.reads[hid];
-                        L.r = R.r;
+                        L.r = hid;  // the list entry (a helper gets it with the subtree)
                         L.m = R.m;
                         L.z = R.z;
                         L.B = R.B;
@@ -405,8 +462,14 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
                 }
             }
             if (__ballot_sync(FULL, L.phase != PH_IDLE && L.phase != PH_FREE) == 0) {
-                __nanosleep(500);
-                idle_trips++;  // about 4 s of trips with nothing to do ends the warp (a task that never came)
+                // back off (0.25 to 16 us) so that idle warps leave the ring's
+                // counters to the lanes that publish and take tasks; 4 s without
+                // work ends the warp (a task that never came)
+                const unsigned long long now = global_ns();
+                if (idle_trips == 0) idle_since = now;
+                idle_expired = __shfl_sync(FULL, now - idle_since > 4000000000ull ? 1u : 0u, 0) != 0;
+                __nanosleep(256u << min(idle_trips, 6u));
+                idle_trips++;
             } else {
                 idle_trips = 0;
             }
@@ -414,6 +477,11 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
             idle_trips = 0;
         }
         if (__ballot_sync(FULL, L.phase != PH_FREE) == 0) break;
+    }
+    const uint32_t wt = __reduce_add_sync(FULL, trips), wb = __reduce_add_sync(FULL, busy);
+    if (lane == 0) {
+        atomicAdd(&H.hdr->lane_trips, static_cast<unsigned long long>(wt));
+        atomicAdd(&H.hdr->busy_trips, static_cast<unsigned long long>(wb));
     }
 }
 
@@ -799,7 +867,8 @@ static cudaError_t launch_cap(const DIndex &X, const ReadBatch &rb, uint32_t n, 
         if (pp.heavy.hdr) {  // the reads handed over, one deepening pass per launch over the whole GPU
             int hb = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hb, aln_heavy_pass_kernel<CAP, SCORE>, kThreads, 0);
-            const unsigned hgrid = static_cast<unsigned>(sms * (hb > 0 ? hb : 1));
+            // the ring holds at most 2 entries per thread of the grid (the pass kernel's low-water mark)
+            const unsigned hgrid = min(static_cast<unsigned>(sms * (hb > 0 ? hb : 1)), kHeavyPool / (2u * kThreads));
             aln_heavy_start_kernel<<<kHeavyReads, 128, 0, st>>>(pp, dbp, X.t[0].n);
             for (uint32_t pass = 0; pass < kHeavyPasses; pass++) {
                 aln_heavy_pass_kernel<CAP, SCORE><<<hgrid, kThreads, 0, st>>>(X, rb, pp, dbp);

@@ -54,14 +54,21 @@ constexpr uint32_t kHeavySlots = 1024;     // candidate hash slots per read and 
 constexpr uint32_t kHeavyPool = 1u << 20;  // task ring capacity
 constexpr uint32_t kHeavyPasses = ALN_HEAVY_PASSES;  // deepening passes launched (enough for z <= 7)
 
-struct HeavyHdr {   // 256 bytes
+struct HeavyHdr {   // 512 bytes: the ring's hot counters on 128-byte lines of their own
     uint32_t n_heavy;      // reads handed over (may pass kHeavyReads: those stay in the first phase)
-    uint32_t head, tail;   // task ring tickets: taken, published
-    uint32_t outstanding;  // tasks of the current pass not yet finished
+    uint32_t pad0;
     unsigned long long expansions;  // node expansions made by the heavy phase's tasks (a statistic)
-    uint32_t pad[58];
+    unsigned long long lane_trips;  // lane trips of the pass kernels, and those with a task (statistics)
+    unsigned long long busy_trips;
+    uint32_t pad1[24];
+    uint32_t head;         // task ring ticket: taken
+    uint32_t pad2[31];
+    uint32_t tail;         // task ring ticket: published
+    uint32_t pad3[31];
+    uint32_t outstanding;  // tasks of the current pass not yet finished
+    uint32_t pad4[31];
 };
-static_assert(sizeof(HeavyHdr) == 256, "heavy header layout");
+static_assert(sizeof(HeavyHdr) == 512, "heavy header layout");
 struct HeavyRead {  // 64 bytes
     uint32_t r, B, z, m;   // read index, pass budget, difference limit, length
     uint32_t state;        // 0 searching, 1 result written
