@@ -34,7 +34,12 @@ BYTES_PER_LOOKUP = 64
 # summaries under profiles/ give the command).  Used only while the kernel
 # sources hash to the value they had at capture time.
 KERNEL_SOURCES = ("aln_device.cuh", "aln_search.cuh", "aln_flat.cuh", "aln_kernels.cu")
-TRAFFIC_CAPTURE = {}  # workload -> {"src_sha256_16": ..., "dram_bytes_per_read": ...}
+TRAFFIC_CAPTURE = {  # workload -> capture; the profile summaries give the commands
+    # 300 000 of the 1 M reads: 6.778 GB read + 0.254 GB written in one launch
+    "chr100": {"src_sha256_16": "0c96d042ff82cfd9", "dram_bytes_per_read": 23441},
+    # the first 200 000 reads of the 1 M-read paired batch: 143.55 GB + 1.06 GB
+    "human_pairs": {"src_sha256_16": "0c96d042ff82cfd9", "dram_bytes_per_read": 723067},
+}
 L2_BYTES = 126 << 20  # GB300 L2 (cudaDevAttrL2CacheSize reports 126 MiB)
 
 
@@ -680,11 +685,12 @@ def run_reference(args):
     v = per_step * args.steps / dt
     sample = f"{per_step} seeded reads per step of the {w.reads.n}-read batch"
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "reads/s", "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "reads/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": workload_config(args.workload, w, per_step, 1, mode="oracle (CPU)"),
-        "cpu_baseline": {"value": v, "unit": "reads/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "reads/s", "cores": threads, "kind": "oracle", "sample": sample,
+                         "where": "rank 0's host cores; no GPU is used"},
         "e2e": {"value": v, "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
