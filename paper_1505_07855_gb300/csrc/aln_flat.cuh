@@ -693,15 +693,7 @@ struct FlatLane {
         unsigned heavym = __ballot_sync(FULL, can_give && (role == ROLE_HELP || work > help_after));
         unsigned freem = __ballot_sync(FULL, phase == PH_FREE);
         unsigned idlem = __ballot_sync(FULL, phase == PH_IDLE && heavy_seen);
-#ifdef ALN_STRAGGLER_OWNERS
-        // the queue is empty for good and the warp works on at most a few reads
-        // of its own: those are the batch's tail and may be handed over
-        if (freem && __popc(__ballot_sync(FULL, role == ROLE_OWN && (phase == PH_DFS || phase == PH_WAIT))) <=
-                         ALN_STRAGGLER_OWNERS)
-            flags |= kFlagDrained;
-#else
         if (freem) flags |= kFlagDrained;  // the queue is empty for good: heavy reads may be handed over
-#endif
         heavy_seen = heavym != 0;
         while (freem && donm) {
             const uint32_t rcv = __ffs(freem) - 1, dnr = __ffs(donm) - 1;
