@@ -281,10 +281,13 @@ typedef struct {
  * from the queue the same way without searching it, so every read gets a
  * result; the binding turns the status bit into ALN_ELIMIT.
  * Persistent mode first computes every read's D array in a pre-pass and visits
- * reads in decreasing order of their lower bound; reads that pass
- * params.heavy_after expansions are then searched by the heavy phase, one
- * deepening pass per launch with every lane of the GPU sharing their subtrees
- * through a task ring.  Its scratch is out->scratch
+ * reads in decreasing order of their lower bound; in the batch's tail (the
+ * read queue empty) reads past params.heavy_after expansions of their owner
+ * lane are handed to the heavy phase (at most 2048 per call), which searches
+ * them from the deepening pass they were in, one pass per launch, with every
+ * lane of the GPU sharing their subtrees through a task ring; it adds
+ * 1 + 2 * ALN_HEAVY_PASSES launches to every persistent call with scratch
+ * (they return at once when no read was handed over).  Its scratch is out->scratch
  * if given, else a block from a memory pool owned by the device index,
  * allocated and freed in stream order by the call.  While stream is being
  * captured into a graph without out->scratch (or if the pool cannot serve) the
