@@ -186,7 +186,8 @@ def oracle_sample(w, n_sample, threads, seed=7):
     return ox, idx, ro, ho, look, t_index, t_align
 
 
-def serving_phase(aln, dix, w, lam, seconds, seed=5, text_note="the 100 Mbp bench text stands in for the 3.1 Gbp one"):
+def serving_phase(aln, dix, w, lam, seconds, seed=5, text_note="the 100 Mbp bench text stands in for the 3.1 Gbp one",
+                  slots=3, batch_reads=1 << 19):
     """Poisson request stream on the resident index: request sizes log-uniform on
     [1, 100000] reads, lengths uniform over 50..250 bp, z = min(6, ceil(0.04 len)),
     errors as the tiny36 recipe; reads are cut from a pre-simulated pool."""
@@ -199,7 +200,7 @@ def serving_phase(aln, dix, w, lam, seconds, seed=5, text_note="the 100 Mbp benc
     rng = np.random.default_rng(seed)
     params = aln.Params(z=6, max_gapo=w.params["max_gapo"], max_gape=w.params["max_gape"],
                         seed_len=0, seed_z=0, indel_end_skip=5, hit_cap=8, mode=aln.MODE_PERSISTENT)
-    srv = aln.Server(dix, params, n_slots=3, max_batch_reads=1 << 19, coalesce_us=500)
+    srv = aln.Server(dix, params, n_slots=slots, max_batch_reads=batch_reads, coalesce_us=500)
     done, lock = [], threading.Lock()
     pending = []
     stop = threading.Event()
@@ -249,7 +250,7 @@ def serving_phase(aln, dix, w, lam, seconds, seed=5, text_note="the 100 Mbp benc
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p95_ms": float(np.percentile(lat, 95)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
-            "batches": st["batches"], "slots": st["n_slots"], "text": text_note}
+            "batches": st["batches"], "slots": st["n_slots"], "max_batch_reads": batch_reads, "text": text_note}
 
 
 def _levenshtein(a, b):
@@ -611,7 +612,8 @@ def human_phase(args, aln, torch, dev, stream, flush):
     # serving on the resident index while the oracle index may still be building
     if args.human_serve_seconds > 0:
         out["serving"] = serving_phase(aln, dix, mixed, args.human_serve_lambda, args.human_serve_seconds,
-                                       text_note="the 3.1 Gbp text, resident")
+                                       text_note="the 3.1 Gbp text, resident", slots=args.serve_slots,
+                                       batch_reads=args.serve_batch_reads)
     # oracle parity: a seeded 1 % of each batch plus every read with a flag
     if not args.no_oracle:
         th.join()
@@ -995,7 +997,8 @@ def run_gpu(args):
         line["parity"]["positions_bit_exact"] = bool(okp)
         line["parity"]["positions_hits_checked"] = int(sel_hits.size)
     if args.serve_seconds > 0:
-        line["serving"] = serving_phase(aln, dix, w, args.serve_lambda, args.serve_seconds)
+        line["serving"] = serving_phase(aln, dix, w, args.serve_lambda, args.serve_seconds, slots=args.serve_slots,
+                                        batch_reads=args.serve_batch_reads)
         line["p99_ms"] = line["serving"]["p99_ms"]
     if args.human and ws == 1:
         args._probes = probes
@@ -1036,6 +1039,8 @@ def main():
     ap.add_argument("--reads", type=int, default=0, help="use only the first N reads (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-lambda", type=float, default=100.0)
+    ap.add_argument("--serve-slots", type=int, default=3, help="server: batches in flight")
+    ap.add_argument("--serve-batch-reads", type=int, default=1 << 19, help="server: reads per batch")
     ap.add_argument("--human", type=int, default=1,
                     help="1: also run the 3.1 Gbp paired and mixed-length batches, oracle-checked, and serving on it")
     ap.add_argument("--human-ref", type=int, default=0, help="human-scale text length (default 3.1 Gbp)")
