@@ -313,8 +313,10 @@ uint64_t aln_search_scratch_bytes(uint32_t n_reads);
  * of a sample batch (device memory, laid out as for aln_search; scratch
  * receives its results): every resident-blocks-per-SM value from 1 to what
  * fits for every shared-memory stack depth of ALN_SMEM_STACK_CHOICES (one
- * warm-up run per depth); writes the fastest blocks_per_sm and smem_stack into
- * params (its time in *best_ms, may be NULL).  The remaining fields of params
+ * warm-up run per depth, two timed runs per candidate, a candidate counting by
+ * its slower run); writes into params the fastest blocks_per_sm and smem_stack
+ * if they beat the default (every block that fits, 8 stack entries) by more
+ * than 5 %, else the default (its time in *best_ms, may be NULL).  The remaining fields of params
  * are used as given: help_after and heavy_after are not tuned (a sample's
  * tail says little about a batch's, and lanes that help a read early keep its
  * owner's expansions below heavy_after, so that it never reaches the heavy

@@ -350,10 +350,11 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
             fetch4(X, fr, lo4, hi4);
             L.apply(X, lo4, hi4);
         }
-        // the ring runs low: task owners give their bottom stack entries back to
-        // it (its level read by one lane, the tickets taken once per warp)
-        const bool can_push = L.role == ROLE_OWN && L.phase == PH_DFS &&
-                              (L.sp - L.base >= 2 || (L.sp - L.base >= 1 && L.has_next));
+        // the ring runs low: lanes give their bottom stack entries back to it (its
+        // level read by one lane, the tickets taken once per warp); helpers too,
+        // or the subtrees a warp's idle lanes take from its owners could never
+        // reach other warps (L.r holds the read's list entry either way)
+        const bool can_push = L.phase == PH_DFS && (L.sp - L.base >= 2 || (L.sp - L.base >= 1 && L.has_next));
         const unsigned pushers = __ballot_sync(FULL, can_push);
         if (pushers) {
             const uint32_t src = __ffs(pushers) - 1;
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, ALN_PERSISTENT_MIN_BLOCKS) aln_heavy
                 L.base++;
                 HeavyTask task;
                 task.node = e;
-                task.hid = hid;
+                task.hid = L.r;
                 task.s = L.s;
                 task.pad0 = task.pad1 = 0;
                 H.pool[t % kHeavyPool] = task;
@@ -719,6 +720,8 @@ __global__ void aln_heavy_decide_kernel(SearchParams p, const uint2 *dbp, uint32
     res[R->r] = out;
     R->state = 1;
 }
+
+// ---------------------------------------------------------------- end of the heavy phase
 
 #ifdef ALN_STATS
 cudaError_t debug_stats(unsigned long long *out, int reset) {
