@@ -9,7 +9,11 @@ repeat families), 1 M single-end 100 bp reads (substitutions 0.5 % -> 2 %,
 A step is one aln_search over the whole 1 M-read batch (both strands, D scans,
 backtracking search, hit reduction).  The headline is the persistent (batched)
 form; the plain one-launch-per-batch form is timed beside it.  L2 is flushed
-(a 512 MiB write) before every timed step.  `--impl reference` times the CPU
+(a 512 MiB write) before every timed step.  Then (unless `--human 0`) the
+3.1 Gbp text: its index built on the GPU, a 1 M-read paired batch and a 1 M-read
+mixed-length batch (autotuned, replayed from a CUDA graph), each persistent
+against plain and checked against the oracle on a seeded 1 % plus every flagged
+read, and serving on the resident text.  `--impl reference` times the CPU
 oracle on bounded samples of the same workload instead.
 """
 from __future__ import annotations
@@ -1039,7 +1043,7 @@ def main():
     ap.add_argument("--kmer-k", type=int, default=10)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--work-limit", type=int, default=0, help="node expansions per read (0 = library default)")
-    ap.add_argument("--autotune", action="store_true", help="choose blocks per SM with aln_autotune first")
+    ap.add_argument("--autotune", action="store_true", help="choose blocks per SM and stack depth with aln_autotune first")
     ap.add_argument("--index-cache", default="", help="load the index image from this file, or build and save it")
     ap.add_argument("--graph", action="store_true", help="time the persistent form as CUDA-graph replays")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
