@@ -50,3 +50,25 @@ def test_partition_range_covers_the_batch_once(n, ws):
     assert all(ranges[i][1] == ranges[i + 1][0] for i in range(ws - 1))
     sizes = np.array([hi - lo for lo, hi in ranges])
     assert sizes.min() >= 0 and sizes.max() - sizes.min() <= 1
+
+
+def test_gpus_n_relaunches_under_torchrun_and_rank0_alone_prints():
+    """`bench.py --gpus 2` starts itself again under torch.distributed.run with two
+    ranks; in the reference arm rank 0 alone runs the oracle and prints the one
+    JSON line (the other rank exits 0 without work)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR",
+                                                            "MASTER_PORT")}
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--workload", "tiny36", "--steps", "1", "--warmup", "0", "--ref-sample", "200"],
+                         cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["config"]["workload"] == "tiny36"
